@@ -1,0 +1,183 @@
+/*
+ * band_bidiag.h -- C ABI of the GB300 (sm_103a) band -> bidiagonal reducer.
+ *
+ * The library reduces an upper-banded n x n matrix A of bandwidth b to an
+ * upper bidiagonal B = Q^T A P (Q, P orthogonal) by Householder bulge
+ * chasing with successive bandwidth reduction: the second stage of the
+ * three-stage SVD (arXiv 2510.12705, Section III, Algorithms 1 and 2).
+ * B has the same singular values as A; only d = diag(B) and
+ * e = superdiag(B) are returned (no singular vectors).
+ *
+ * Conventions shared by every entry point
+ *   - Band storage (LAPACK 'U', 0-based, column-major):
+ *         A[i][j] = band[(b + i - j) + j * ldab]   for 0 <= j - i <= b,
+ *     ldab >= b + 1.  Entries of the first b columns that lie above row 0
+ *     are ignored.  The input band is never modified.
+ *   - Element type: BB_F64 (double) or BB_F32 (float) for band, d and e.
+ *     BB_F32 stores and updates in FP32 and generates every reflector
+ *     (norm, beta, tau) in FP64 from the FP32 data (the precision split).
+ *   - Device pointers: band, d_out (n elements), e_out (n-1 elements; may be
+ *     NULL when n == 1) and workspace are CUDA device pointers on the
+ *     current device; the caller owns them.  `stream` is a cudaStream_t
+ *     (NULL = legacy default stream).  All work is enqueued on `stream`
+ *     and the call returns without synchronising (except where stated).
+ *   - b >= n is treated as b = n - 1.  b = 0 gives d = diag(A), e = 0;
+ *     b = 1 copies the two diagonals.
+ *   - Signs of d and e are those the reflectors produce (singular values are
+ *     sign-invariant).
+ *   - Return value: BB_OK or a BB_ERR_* code for errors detectable on the
+ *     host (arguments, allocation, launch).  Errors found on the device
+ *     (a bounded wait that ran out, non-finite input) are recorded in a
+ *     sticky per-device status word read by bb_device_status().
+ */
+#ifndef BAND_BIDIAG_H
+#define BAND_BIDIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes (device status bits use the same values as flags: 1 << code) */
+#define BB_OK 0
+#define BB_ERR_ARG 1          /* invalid argument (n < 1, b < 0, ldab < b+1, NULL pointer, dtype, tuning) */
+#define BB_ERR_ALLOC 2        /* stream-ordered allocation of the internal workspace failed */
+#define BB_ERR_LAUNCH 3       /* a kernel launch or a CUDA call failed */
+#define BB_ERR_TIMEOUT 4      /* device: a bounded spin-wait saw no progress within the time limit */
+#define BB_ERR_NONFINITE 5    /* device: the input band holds NaN or Inf */
+#define BB_ERR_WORKSPACE 6    /* caller workspace smaller than the size query returned */
+#define BB_ERR_UNSUPPORTED 7  /* configuration outside the compiled kernels (shared memory, n >= 2^20) */
+
+#define BB_F32 0
+#define BB_F64 1
+
+/* tuning flags */
+#define BB_FLAG_INJECT_STALL 0x100   /* fault injection for tests: sweep 0 never reports
+                                        progress, so the bounded waits of the other sweeps
+                                        run out and the call records BB_ERR_TIMEOUT */
+
+/*
+ * Kernel hyperparameters (Section IV-C): zero selects the built-in default.
+ *   tw               inner tilewidth TW: bandwidth removed per stage (1..32)
+ *   tpb              threads per bulge (CTA size: 64, 128, 256 or 512)
+ *   sweeps_in_flight persistent CTAs, i.e. sweeps processed concurrently
+ *                    (the paper's "max blocks"); capped at what fits on the GPU
+ *   flags            BB_FLAG_*
+ *   timeout_s        limit on every device spin-wait without progress, seconds
+ *                    (default 5 s)
+ *   ev_start/ev_stop optional cudaEvent_t handles (NULL = none): recorded on the
+ *                    call's stream immediately before and after the persistent
+ *                    bulge-chasing kernel, so a caller can time that kernel alone
+ */
+typedef struct {
+    int tw;
+    int tpb;
+    int sweeps_in_flight;
+    int flags;
+    double timeout_s;
+    void *ev_start;
+    void *ev_stop;
+} bb_tuning;
+
+/* one problem of a batch: fields as in band_to_bidiag() */
+typedef struct {
+    int64_t n;
+    int64_t b;
+    const void *band;
+    int64_t ldab;
+    void *d_out;
+    void *e_out;
+} bb_problem;
+
+/*
+ * band_to_bidiag -- reduce one band matrix (Algorithm 1 over all stages,
+ * one persistent launch).  The workspace (working band with fill rows of
+ * height b + 2 TW + 1, Section V storage format, plus progress counters) is
+ * taken from CUDA's stream-ordered allocator on `stream` and released on it.
+ */
+int band_to_bidiag(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab,
+                   void *d_out, void *e_out, void *stream);
+
+/*
+ * band_to_bidiag_ex -- as band_to_bidiag with explicit tuning (NULL = default)
+ * and an optional caller workspace (device, 256-byte aligned, at least
+ * band_to_bidiag_workspace_size() bytes; NULL = stream-ordered allocation).
+ * A caller workspace must not be used by two calls that overlap on the GPU.
+ */
+int band_to_bidiag_ex(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab,
+                      void *d_out, void *e_out, const bb_tuning *tuning,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* bytes of workspace band_to_bidiag_ex needs for this problem and tuning */
+size_t band_to_bidiag_workspace_size(int64_t n, int64_t b, int dtype, const bb_tuning *tuning);
+
+/*
+ * band_to_bidiag_host -- end-to-end call on HOST buffers: copies the band
+ * (ldab x n elements) to the device, reduces it, copies d and e back and
+ * synchronises `stream`.  band, d_out, e_out are host pointers (pinned
+ * memory gives the fastest copies).  Device memory comes from the
+ * stream-ordered allocator.  Returns the first host- or device-side error
+ * (the device status is read and cleared).
+ */
+int band_to_bidiag_host(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab,
+                        void *d_out, void *e_out, const bb_tuning *tuning, void *stream);
+
+/*
+ * Batched reduction of many independent band matrices of uneven n and b in
+ * ONE persistent launch (plus a pack and an extract kernel).  A plan holds
+ * the problem table in pinned host memory; bb_batch_execute enqueues only
+ * stream operations (a host-to-device copy of the table, memsets and three
+ * kernels), so it can be captured into a CUDA graph and replayed, as long as
+ * the problems' pointers stay valid.
+ */
+typedef struct bb_batch_plan bb_batch_plan;
+bb_batch_plan *bb_batch_plan_create(int count, const bb_problem *problems, int dtype,
+                                    const bb_tuning *tuning);
+size_t bb_batch_plan_workspace_size(const bb_batch_plan *plan);
+int bb_batch_execute(const bb_batch_plan *plan, void *workspace, size_t workspace_bytes,
+                     void *stream);
+void bb_batch_plan_destroy(bb_batch_plan *plan);
+
+/*
+ * Device status: synchronises `stream`, returns the sticky status word of the
+ * current device (bit (1 << code) set for each device-side error code seen
+ * since the last reset) and clears it when `reset` is non-zero.
+ */
+int bb_device_status(void *stream, int reset);
+
+/* human-readable name of a status code */
+const char *bb_status_string(int code);
+
+/*
+ * Work model of the executed schedule (host only, no GPU needed): number of
+ * stages and row-bulges, floating-point operations (4 m per reflector
+ * application to a row or column of length m, plus generation), and
+ * elements touched (|right panel U left panel| per row-bulge; algorithmic
+ * bytes = 2 * elements * sizeof(element), one read and one write).
+ */
+int bb_schedule_counts(int64_t n, int64_t b, int tw, int64_t *stages, int64_t *steps,
+                       double *flops, double *elements);
+
+/* built-in default tuning for (n, b, dtype) */
+int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning *out);
+
+/*
+ * Microbenchmarks for the roofline denominators, run on `stream` of the
+ * current device (synchronous):
+ *   bb_measure_l2_bandwidth: read+write bytes/s of a copy kernel over a
+ *       `bytes`-sized buffer pair that stays resident in L2, repeated `reps`
+ *       times; returns GB/s.
+ *   bb_measure_fma_peak: FMA throughput of independent FMA chains in every
+ *       thread of a full-GPU grid; dtype BB_F32 or BB_F64; returns GFLOP/s
+ *       (2 flops per FMA).
+ * Both return a negative value on failure.
+ */
+double bb_measure_l2_bandwidth(size_t bytes, int reps, void *stream);
+double bb_measure_fma_peak(int dtype, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAND_BIDIAG_H */

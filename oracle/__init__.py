@@ -129,8 +129,8 @@ def bidiag_sigma(d: np.ndarray, e: np.ndarray, method: str = "auto") -> np.ndarr
     "bisect": our own Sturm-count bisection on the 2n x 2n Golub-Kahan
     tridiagonal (zero diagonal, off-diagonal d0, e0, d1, ...), whose
     eigenvalues are +-sigma.  "lapack": the same Golub-Kahan matrix through
-    scipy's tridiagonal eigensolver (LAPACK stemr), used as a library step for
-    large n.  "auto" picks bisection up to n = 2048.
+    scipy's tridiagonal eigensolver (LAPACK sterf, root-free QR), used as a
+    library step for large n.  "auto" picks bisection up to n = 2048.
     """
     d = np.ascontiguousarray(d, dtype=np.float64)
     e = np.ascontiguousarray(e, dtype=np.float64)
@@ -152,7 +152,7 @@ def bidiag_sigma(d: np.ndarray, e: np.ndarray, method: str = "auto") -> np.ndarr
         off = np.zeros(2 * n - 1)
         off[0::2] = d
         off[1::2] = e
-        w = eigvalsh_tridiagonal(np.zeros(2 * n), off, lapack_driver="stemr")
+        w = eigvalsh_tridiagonal(np.zeros(2 * n), off, lapack_driver="sterf")
         return np.sort(np.abs(w[n:]))[::-1]
     raise ValueError(method)
 

@@ -1,0 +1,274 @@
+"""GB300 (sm_103a) band -> bidiagonal reduction: thin binding over the C ABI.
+
+Every step of the reduction runs in the CUDA kernels of ``libbandbidiag.so``
+(``include/band_bidiag.h``); this module only marshals arguments.  PyTorch is
+used for device memory and streams.  The functions keep the C names:
+
+    band_to_bidiag(band, b, d_out, e_out, stream=None)
+    band_to_bidiag_ex(band, b, d_out, e_out, tuning=None, workspace=None, stream=None)
+    band_to_bidiag_host(band_np, b, tuning=None) -> (d, e)
+    band_to_bidiag_workspace_size(n, b, dtype, tuning=None)
+    BatchPlan(problems, dtype, tuning)       # bb_batch_plan_*
+    bb_device_status(stream=None, reset=True)
+    bb_schedule_counts(n, b, tw), bb_default_tuning(n, b, dtype)
+    bb_measure_l2_bandwidth(bytes, reps), bb_measure_fma_peak(dtype)
+
+Band tensors use LAPACK 'U' band storage seen as a row-major (n, ldab)
+array: row j holds column j of the band, A[i, j] = band[j, b + i - j].
+There is no CPU fallback: without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbandbidiag.so")
+
+BB_OK = 0
+BB_ERR_ARG = 1
+BB_ERR_ALLOC = 2
+BB_ERR_LAUNCH = 3
+BB_ERR_TIMEOUT = 4
+BB_ERR_NONFINITE = 5
+BB_ERR_WORKSPACE = 6
+BB_ERR_UNSUPPORTED = 7
+BB_F32 = 0
+BB_F64 = 1
+BB_FLAG_INJECT_STALL = 0x100
+
+_lib = None
+
+
+class BBError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})" if what else status_string(code))
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tw", ctypes.c_int), ("tpb", ctypes.c_int), ("sweeps_in_flight", ctypes.c_int),
+                ("flags", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("ev_start", ctypes.c_void_p), ("ev_stop", ctypes.c_void_p)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("b", ctypes.c_int64), ("band", ctypes.c_void_p),
+                ("ldab", ctypes.c_int64), ("d_out", ctypes.c_void_p), ("e_out", ctypes.c_void_p)]
+
+
+def lib():
+    """Load the compiled library; raise if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2510_12705_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        i64, vp, ci, sz = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        tp = ctypes.POINTER(Tuning)
+        sig = {
+            "band_to_bidiag": (ci, [i64, i64, ci, vp, i64, vp, vp, vp]),
+            "band_to_bidiag_ex": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, vp, sz, vp]),
+            "band_to_bidiag_workspace_size": (sz, [i64, i64, ci, tp]),
+            "band_to_bidiag_host": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, vp]),
+            "bb_batch_plan_create": (vp, [ci, ctypes.POINTER(Problem), ci, tp]),
+            "bb_batch_plan_workspace_size": (sz, [vp]),
+            "bb_batch_execute": (ci, [vp, vp, sz, vp]),
+            "bb_batch_plan_destroy": (None, [vp]),
+            "bb_device_status": (ci, [vp, ci]),
+            "bb_status_string": (ctypes.c_char_p, [ci]),
+            "bb_schedule_counts": (ci, [i64, i64, ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+            "bb_default_tuning": (ci, [i64, i64, ci, tp]),
+            "bb_measure_l2_bandwidth": (ctypes.c_double, [sz, ci, vp]),
+            "bb_measure_fma_peak": (ctypes.c_double, [ci, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().bb_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != BB_OK:
+        raise BBError(code, what)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t == torch.float64:
+        return BB_F64
+    if t == torch.float32:
+        return BB_F32
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def _tuning_ptr(tuning):
+    if tuning is None:
+        return None
+    if isinstance(tuning, dict):
+        t = Tuning()
+        for k, v in tuning.items():
+            setattr(t, k, v)
+        tuning = t
+    return ctypes.byref(tuning)
+
+
+def _check_band(band, d_out, e_out):
+    n, ldab = band.shape
+    if not (band.is_cuda and d_out.is_cuda and (n == 1 or e_out.is_cuda)):
+        raise ValueError("band, d_out and e_out must be CUDA tensors")
+    if not band.is_contiguous():
+        raise ValueError("band must be contiguous (n, ldab)")
+    if d_out.dtype != band.dtype or (n > 1 and e_out.dtype != band.dtype):
+        raise ValueError("d_out / e_out must have the band's dtype")
+    if d_out.numel() < n or (n > 1 and e_out.numel() < n - 1):
+        raise ValueError("d_out needs n and e_out n-1 elements")
+    return n, ldab
+
+
+def band_to_bidiag(band, b: int, d_out, e_out, stream=None) -> None:
+    """Reduce ``band`` (CUDA tensor (n, ldab), float32/float64) into d_out, e_out."""
+    n, ldab = _check_band(band, d_out, e_out)
+    rc = lib().band_to_bidiag(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab,
+                              d_out.data_ptr(), e_out.data_ptr() if n > 1 else None,
+                              _stream_handle(stream))
+    _check(rc, "band_to_bidiag")
+
+
+def band_to_bidiag_ex(band, b: int, d_out, e_out, tuning=None, workspace=None, stream=None):
+    n, ldab = _check_band(band, d_out, e_out)
+    ws_ptr, ws_bytes = (None, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    rc = lib().band_to_bidiag_ex(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab,
+                                 d_out.data_ptr(), e_out.data_ptr() if n > 1 else None,
+                                 _tuning_ptr(tuning), ws_ptr, ws_bytes, _stream_handle(stream))
+    _check(rc, "band_to_bidiag_ex")
+
+
+def band_to_bidiag_workspace_size(n: int, b: int, dtype: int, tuning=None) -> int:
+    return int(lib().band_to_bidiag_workspace_size(n, b, dtype, _tuning_ptr(tuning)))
+
+
+def band_to_bidiag_host(band, b: int, tuning=None, stream=None, out=None):
+    """End-to-end call on host numpy arrays (pinned if possible): returns (d, e)."""
+    import numpy as np
+    band = np.ascontiguousarray(band)
+    n, ldab = band.shape
+    code = BB_F64 if band.dtype == np.float64 else BB_F32
+    if out is None:
+        d = np.empty(n, dtype=band.dtype)
+        e = np.empty(max(n - 1, 1), dtype=band.dtype)
+    else:
+        d, e = out
+    rc = lib().band_to_bidiag_host(n, b, code, band.ctypes.data, ldab, d.ctypes.data,
+                                   e.ctypes.data, _tuning_ptr(tuning), _stream_handle(stream))
+    _check(rc, "band_to_bidiag_host")
+    return d, e[: n - 1]
+
+
+def band_to_bidiag_host_ptr(n: int, b: int, dtype: int, band_ptr: int, ldab: int, d_ptr: int,
+                            e_ptr: int, tuning=None, stream=None) -> int:
+    """Raw-pointer form of band_to_bidiag_host (e.g. pinned torch CPU tensors)."""
+    return lib().band_to_bidiag_host(n, b, dtype, band_ptr, ldab, d_ptr, e_ptr,
+                                     _tuning_ptr(tuning), _stream_handle(stream))
+
+
+def bb_device_status(stream=None, reset: bool = True) -> int:
+    return int(lib().bb_device_status(_stream_handle(stream), 1 if reset else 0))
+
+
+def status_bits(word: int) -> list[int]:
+    return [c for c in range(1, 16) if word & (1 << c)]
+
+
+def bb_default_tuning(n: int, b: int, dtype: int) -> Tuning:
+    t = Tuning()
+    _check(lib().bb_default_tuning(n, b, dtype, ctypes.byref(t)), "bb_default_tuning")
+    return t
+
+
+@dataclass
+class ScheduleCounts:
+    stages: int
+    steps: int
+    flops: float
+    elements: float
+
+    def bytes(self, elem_size: int) -> float:
+        """Algorithmic bytes: every touched element read once and written once."""
+        return 2.0 * self.elements * elem_size
+
+
+def bb_schedule_counts(n: int, b: int, tw: int) -> ScheduleCounts:
+    st, sp = ctypes.c_int64(), ctypes.c_int64()
+    fl, el = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bb_schedule_counts(n, b, tw, ctypes.byref(st), ctypes.byref(sp),
+                                    ctypes.byref(fl), ctypes.byref(el)), "bb_schedule_counts")
+    return ScheduleCounts(st.value, sp.value, fl.value, el.value)
+
+
+def bb_measure_l2_bandwidth(nbytes: int = 32 << 20, reps: int = 200, stream=None) -> float:
+    return float(lib().bb_measure_l2_bandwidth(nbytes, reps, _stream_handle(stream)))
+
+
+def bb_measure_fma_peak(dtype: int, stream=None) -> float:
+    return float(lib().bb_measure_fma_peak(dtype, _stream_handle(stream)))
+
+
+class BatchPlan:
+    """bb_batch_plan: many band problems reduced in one persistent launch.
+
+    ``problems``: list of (band, b, d_out, e_out) CUDA tensors of one dtype.
+    ``execute(workspace, stream)`` only enqueues stream work, so it can be
+    captured into a CUDA graph (``torch.cuda.CUDAGraph``) and replayed.
+    """
+
+    def __init__(self, problems, tuning=None):
+        self._keep = problems
+        dt = problems[0][0].dtype
+        self.dtype = _dtype_code(dt)
+        arr = (Problem * len(problems))()
+        for i, (band, b, d, e) in enumerate(problems):
+            n, ldab = _check_band(band, d, e)
+            if band.dtype != dt:
+                raise ValueError("all problems of a batch share one dtype")
+            arr[i] = Problem(n, b, band.data_ptr(), ldab, d.data_ptr(),
+                             e.data_ptr() if n > 1 else None)
+        self._arr = arr
+        self._plan = lib().bb_batch_plan_create(len(problems), arr, self.dtype, _tuning_ptr(tuning))
+        if not self._plan:
+            raise BBError(BB_ERR_ARG, "bb_batch_plan_create")
+        self.workspace_bytes = int(lib().bb_batch_plan_workspace_size(self._plan))
+
+    def execute(self, workspace, stream=None):
+        rc = lib().bb_batch_execute(self._plan, workspace.data_ptr(),
+                                    workspace.numel() * workspace.element_size(),
+                                    _stream_handle(stream))
+        _check(rc, "bb_batch_execute")
+
+    def __del__(self):
+        p = getattr(self, "_plan", None)
+        if p and _lib is not None:
+            _lib.bb_batch_plan_destroy(p)
+            self._plan = None

@@ -1,0 +1,667 @@
+// Band -> bidiagonal reduction by Householder bulge chasing on sm_103a
+// (arXiv 2510.12705, Section III: Algorithm 1 schedule, Algorithm 2 row-bulge).
+//
+// One persistent launch runs every stage of every problem.  CTAs claim tasks
+// (stage, problem, sweep) in order from a global counter; a task runs the
+// row-bulges of one sweep.  Consecutive sweeps of a stage are separated by
+// the dependency distance of Section III-A: sweep R may start row-bulge s
+// once sweep R-1 has finished row-bulge s + L - 1, with L = 2 when the
+// post-stage bandwidth is at least 2 and L = 3 otherwise.  Stage i+1 of a
+// problem starts once all sweeps of stage i have finished.  Because tasks are
+// claimed in order and only wait on earlier tasks, the schedule cannot
+// deadlock however many CTAs are resident.  Every wait is bounded.
+//
+// A row-bulge stages its right panel (rows r0..c+m-1 x columns c..c+m-1) and
+// left panel (rows c..c+m-1 x columns c..jmax) in shared memory, builds each
+// reflector with one warp (FP64 generation), applies it with one thread per
+// row / column, and writes both panels back through L2.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/band_bidiag.h"
+#include "bb_device.cuh"
+
+using namespace bb;
+
+static __device__ unsigned int g_bb_status;   // sticky device status (bits 1 << code)
+
+// ------------------------------------------------------------------ kernels
+
+template <typename T>
+__global__ void pack_kernel(Launch L)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gc = wg; gc < L.total_cols; gc += nw) {
+        const int q = find_problem_by_col(L, gc);
+        const Desc& D = desc_of(L, q);
+        const int j = (int)(gc - D.col_prefix);
+        T* wcol = (T*)L.wbase + D.w_off + (int64_t)j * D.ldw;
+        const T* bcol = (const T*)D.band + (int64_t)j * D.ldab;
+        bool bad = false;
+        for (int off = lane; off < D.ldw; off += 32) {
+            const int i = j - D.top + off;   // matrix row of this slot
+            const int k = j - i;             // superdiagonal offset
+            T v = (T)0;
+            if (i >= 0 && k >= 0 && k <= D.b) {
+                v = bcol[D.b_in - k];
+                bad |= !isfinite(v);
+            }
+            wcol[off] = v;
+        }
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(&L.hdr->err, 1 << 5);
+    }
+}
+
+template <typename T>
+__global__ void extract_kernel(Launch L)
+{
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t gc = t0; gc < L.total_cols; gc += nt) {
+        const int q = find_problem_by_col(L, gc);
+        const Desc& D = desc_of(L, q);
+        const int i = (int)(gc - D.col_prefix);
+        const T* W = (const T*)L.wbase + D.w_off;
+        ((T*)D.d)[i] = W[(int64_t)D.top + (int64_t)i * D.ldw];
+        if (i + 1 < D.n) ((T*)D.e)[i] = W[(int64_t)(D.top - 1) + (int64_t)(i + 1) * D.ldw];
+    }
+    if (t0 == 0) {
+        const int err = L.hdr->err;
+        if (err) atomicOr(&g_bb_status, (unsigned)err);
+    }
+}
+
+// One row-bulge (Algorithm 2) of sweep R, stage (bw, d), on the CTA.
+template <typename T, int MAXM>
+__device__ __forceinline__ void row_bulge(const Desc& D, T* __restrict__ W, int bw, int d, int R,
+                                          int s, T* RP, int rpn, T* LP, T* vR, T* vL, T* tb)
+{
+    const int n = D.n, ldw = D.ldw, top = D.top;
+    const int c = R + (bw - d) + s * bw;
+    const int m = min(d + 1, n - c);
+    const int r0 = (s == 0) ? R : c - bw;
+    const int nr = c + m - r0;                 // rows r0 .. c+m-1
+    const int jmax = min(n - 1, c + m - 1 + bw);
+    const int nc = jmax - c + 1;               // columns c .. jmax
+    const int ro = c - r0;                     // right-panel row of matrix row c
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // stage the right panel (column-major, rows fastest) ...
+    for (int f = tid; f < nr * m; f += nt) {
+        const int k = f / nr, r = f - k * nr;
+        RP[k * rpn + r] = ldcg(W + (int64_t)(c + k) * ldw + (r0 - c - k + top + r));
+    }
+    // ... and the left panel's columns right of the overlap block
+    for (int f = tid; f < (nc - m) * m; f += nt) {
+        const int jj = m + f / m, k = f - (jj - m) * m;
+        LP[jj * MAXM + k] = ldcg(W + (int64_t)(c + jj) * ldw + (top - jj + k));
+    }
+    __syncthreads();
+
+    // right reflector from row r0, applied to rows r0+1 .. c+m-1
+    if (tid < 32) warp_reflector<T>(m, RP, rpn, vR, tb);
+    __syncthreads();
+    {
+        const T tau = tb[0];
+        for (int r = 1 + tid; r < nr; r += nt) {
+            T a[MAXM];
+            T w = (T)0;
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k)
+                if (k < m) { a[k] = RP[k * rpn + r]; w = fma(a[k], vR[k], w); }
+            w *= tau;
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k)
+                if (k < m) RP[k * rpn + r] = fma(-w, vR[k], a[k]);
+        }
+        if (tid < m) RP[tid * rpn] = (tid == 0) ? tb[1] : (T)0;
+    }
+    __syncthreads();
+
+    // overlap block (rows c.., columns c..c+m-1) after the right reflector
+    for (int f = tid; f < m * m; f += nt) {
+        const int kc = f / m, k = f - kc * m;
+        LP[kc * MAXM + k] = RP[kc * rpn + ro + k];
+    }
+    __syncthreads();
+
+    // left reflector from column c, applied to columns c+1 .. jmax
+    if (tid < 32) warp_reflector<T>(m, LP, 1, vL, tb + 2);
+    __syncthreads();
+    {
+        const T tau = tb[2];
+        for (int jj = 1 + tid; jj < nc; jj += nt) {
+            T a[MAXM];
+            T w = (T)0;
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k)
+                if (k < m) { a[k] = LP[jj * MAXM + k]; w = fma(vL[k], a[k], w); }
+            w *= tau;
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k)
+                if (k < m) LP[jj * MAXM + k] = fma(-w, vL[k], a[k]);
+        }
+        if (tid < m) LP[tid] = (tid == 0) ? tb[3] : (T)0;
+    }
+    __syncthreads();
+
+    // write back: right panel rows r0 .. c-1, then the whole left panel
+    for (int f = tid; f < ro * m; f += nt) {
+        const int k = f / ro, r = f - k * ro;
+        stcg(W + (int64_t)(c + k) * ldw + (r0 - c - k + top + r), RP[k * rpn + r]);
+    }
+    for (int f = tid; f < nc * m; f += nt) {
+        const int jj = f / m, k = f - jj * m;
+        stcg(W + (int64_t)(c + jj) * ldw + (top - jj + k), LP[jj * MAXM + k]);
+    }
+}
+
+template <typename T, int MAXM>
+__global__ void __launch_bounds__(512) bulge_kernel(Launch L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* RP = (T*)smem_raw;
+    T* LP = RP + (size_t)MAXM * L.rp_rows;
+    T* vR = LP + (size_t)L.lp_cols * MAXM;
+    T* vL = vR + 64;
+    T* tb = vL + 64;
+    __shared__ int s_task[4];
+    __shared__ int s_ok;         // result of the per-step wait
+    __shared__ int s_stage_ok;   // result of the stage-barrier wait
+    const int tid = threadIdx.x;
+
+    for (;;) {
+        if (tid == 0) {
+            int t = -1;
+            if (!ld_relaxed(&L.hdr->abort)) t = atomicAdd(&L.hdr->claim, 1);
+            if (t >= 0 && t < L.total_tasks) {
+                const int64_t stage = t / L.sweeps_per_stage;
+                const int64_t r = t - stage * L.sweeps_per_stage;
+                const int q = find_problem_by_sweep(L, r);
+                s_task[0] = (int)stage;
+                s_task[1] = q;
+                s_task[2] = (int)(r - desc_of(L, q).sweep_prefix);
+            } else {
+                s_task[0] = -1;
+            }
+        }
+        __syncthreads();
+        const int stage = s_task[0];
+        if (stage < 0) break;
+        const int q = s_task[1], R = s_task[2];
+        const Desc& D = desc_of(L, q);
+        __syncthreads();   // s_task may be rewritten on the next claim
+        if (stage >= D.nstages) continue;
+
+        const int n = D.n;
+        const int bw = stage_bw(D.b, L.tw, stage);
+        const int d = stage_d(bw, L.tw);
+        const int lag = (bw - d >= 2) ? 2 : 3;
+        const int base = stage * PROG_STAGE;
+        int* prog = L.prog + D.prog_off;
+        const int ns = sweep_steps(n, bw, d, R);
+        const int nsp = (R > 0) ? sweep_steps(n, bw, d, R - 1) : 0;
+        T* W = (T*)L.wbase + D.w_off;
+        const bool stall = (L.flags & BB_FLAG_INJECT_STALL) && stage == 0 && R == 0;
+
+        if (tid == 0) {
+            bool ok = true;
+            if (stage > 0) ok = wait_at_least(&L.stage_done[q], stage * (n - 1), L.hdr, L.timeout_ns);
+            s_stage_ok = ok;
+        }
+        __syncthreads();
+        if (!s_stage_ok) break;
+
+        bool ok = true;
+        for (int s = 0; s < ns; ++s) {
+            if (tid == 0) {
+                bool w_ok = true;
+                if (R > 0) w_ok = wait_at_least(&prog[R - 1], base + min(s + lag, nsp), L.hdr, L.timeout_ns);
+                s_ok = w_ok;
+            }
+            __syncthreads();
+            if (!s_ok) { ok = false; break; }
+            row_bulge<T, MAXM>(D, W, bw, d, R, s, RP, L.rp_rows, LP, vR, vL, tb);
+            __syncthreads();
+            if (tid == 0 && !stall) {
+                __threadfence();
+                st_release(&prog[R], base + s + 1);
+            }
+        }
+        if (!ok) break;
+        if (tid == 0 && !stall) {
+            if (ns == 0) st_release(&prog[R], base);
+            __threadfence();
+            atomicAdd(&L.stage_done[q], 1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------- host
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+int clamp_b(int64_t n, int64_t b) { return (int)std::min<int64_t>(b, std::max<int64_t>(n - 1, 0)); }
+
+int num_stages(int b, int tw)
+{
+    int st = 0;
+    for (int bw = b; bw > 1; bw -= std::min(tw, bw - 1)) ++st;
+    return st;
+}
+
+int maxm_for(int tw)
+{
+    if (tw <= 4) return 5;
+    if (tw <= 8) return 9;
+    if (tw <= 16) return 17;
+    return 33;
+}
+
+struct Resolved {
+    int dtype, tw, tpb, sif, flags;
+    unsigned long long timeout_ns;
+    cudaEvent_t ev_start, ev_stop;
+};
+
+bool resolve_tuning(int64_t n, int64_t b, int dtype, const bb_tuning* t, Resolved* r)
+{
+    bb_tuning def;
+    bb_default_tuning(n, b, dtype, &def);
+    r->dtype = dtype;
+    r->tw = (t && t->tw > 0) ? t->tw : def.tw;
+    r->tpb = (t && t->tpb > 0) ? t->tpb : def.tpb;
+    r->sif = (t && t->sweeps_in_flight > 0) ? t->sweeps_in_flight : 0;
+    r->flags = t ? t->flags : 0;
+    const double to = (t && t->timeout_s > 0) ? t->timeout_s : def.timeout_s;
+    r->timeout_ns = (unsigned long long)(to * 1e9);
+    r->ev_start = t ? (cudaEvent_t)t->ev_start : nullptr;
+    r->ev_stop = t ? (cudaEvent_t)t->ev_stop : nullptr;
+    if (r->tw < 1 || r->tw > 32) return false;
+    if (r->tpb != 64 && r->tpb != 128 && r->tpb != 256 && r->tpb != 512) return false;
+    return true;
+}
+
+struct LaunchPlan {
+    Launch L;
+    std::vector<Desc> descs;
+    int esize = 8;
+    int max_stages = 0;
+    int max_b = 0;
+    size_t off_hdr = 0, off_stage = 0, off_prog = 0, off_desc = 0, off_w = 0, bytes = 0;
+    size_t smem = 0;
+    Resolved tune;
+};
+
+// Lay out a launch for `count` problems (host-side planning, no CUDA calls).
+int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* tuning,
+                LaunchPlan* P)
+{
+    if (count < 1 || !probs || (dtype != BB_F32 && dtype != BB_F64)) return BB_ERR_ARG;
+    int64_t nmax = 0, bmax = 0;
+    for (int q = 0; q < count; ++q) {
+        const bb_problem& p = probs[q];
+        if (p.n < 1 || p.b < 0 || p.ldab < p.b + 1 || !p.band || !p.d_out) return BB_ERR_ARG;
+        if (p.n > 1 && !p.e_out) return BB_ERR_ARG;
+        if (p.n >= PROG_STAGE) return BB_ERR_UNSUPPORTED;
+        nmax = std::max(nmax, p.n);
+        bmax = std::max<int64_t>(bmax, clamp_b(p.n, p.b));
+    }
+    if (!resolve_tuning(nmax, bmax, dtype, tuning, &P->tune)) return BB_ERR_ARG;
+    const int tw = P->tune.tw;
+    P->esize = dtype == BB_F64 ? 8 : 4;
+    P->descs.resize(count);
+    int64_t sweep_prefix = 0, col_prefix = 0, welems = 0;
+    int max_stages = 0, max_b = 0;
+    for (int q = 0; q < count; ++q) {
+        const bb_problem& p = probs[q];
+        Desc& D = P->descs[q];
+        std::memset(&D, 0, sizeof(D));
+        D.n = (int)p.n;
+        D.b = clamp_b(p.n, p.b);
+        D.b_in = (int)p.b;
+        D.nstages = num_stages(D.b, tw);
+        D.top = D.b + tw;
+        D.ldw = (int)align_up((size_t)(D.b + 2 * tw + 1), 4);
+        D.w_off = welems;
+        D.prog_off = col_prefix;
+        D.sweep_prefix = sweep_prefix;
+        D.col_prefix = col_prefix;
+        D.band = p.band;
+        D.ldab = p.ldab;
+        D.d = p.d_out;
+        D.e = p.e_out;
+        welems += (int64_t)align_up((size_t)D.ldw * (size_t)D.n * P->esize) / P->esize;
+        sweep_prefix += D.n - 1;
+        col_prefix += D.n;
+        max_stages = std::max(max_stages, D.nstages);
+        max_b = std::max(max_b, D.b);
+    }
+    P->max_stages = max_stages;
+    P->max_b = max_b;
+    size_t off = 0;
+    P->off_hdr = off;   off = align_up(off + sizeof(Header));
+    P->off_stage = off; off = align_up(off + sizeof(int) * (size_t)count);
+    P->off_prog = off;  off = align_up(off + sizeof(int) * (size_t)col_prefix);
+    P->off_desc = off;  off = align_up(off + (count > 1 ? sizeof(Desc) * (size_t)count : 0));
+    P->off_w = off;     off = align_up(off + (size_t)welems * P->esize);
+    P->bytes = off;
+
+    Launch& L = P->L;
+    std::memset(&L, 0, sizeof(L));
+    L.count = count;
+    L.descs = nullptr;
+    L.single = P->descs[0];
+    L.tw = tw;
+    L.sweeps_per_stage = sweep_prefix;
+    L.total_tasks = (int64_t)max_stages * sweep_prefix;
+    L.total_cols = col_prefix;
+    L.timeout_ns = P->tune.timeout_ns;
+    L.flags = P->tune.flags;
+    L.rp_rows = max_b + tw + 1;
+    L.lp_cols = max_b + tw + 1;
+    const int maxm = maxm_for(tw);
+    P->smem = (size_t)P->esize * ((size_t)maxm * L.rp_rows + (size_t)L.lp_cols * maxm + 2 * 64 + 4) + 64;
+    if (L.total_tasks >= (int64_t)INT32_MAX) return BB_ERR_UNSUPPORTED;
+    return BB_OK;
+}
+
+void bind_workspace(LaunchPlan* P, void* ws)
+{
+    char* base = (char*)ws;
+    P->L.hdr = (Header*)(base + P->off_hdr);
+    P->L.stage_done = (int*)(base + P->off_stage);
+    P->L.prog = (int*)(base + P->off_prog);
+    P->L.wbase = base + P->off_w;
+    if (P->L.count > 1) P->L.descs = (const Desc*)(base + P->off_desc);
+}
+
+template <typename T, int MAXM>
+int launch_bulge(const LaunchPlan& P, cudaStream_t st)
+{
+    auto kern = bulge_kernel<T, MAXM>;
+    if (P.smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) != cudaSuccess)
+            return BB_ERR_UNSUPPORTED;
+    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.tune.tpb, P.smem) != cudaSuccess ||
+        per_sm < 1)
+        return BB_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
+    grid = std::min<int64_t>(grid, P.L.total_tasks);
+    if (grid < 1) return BB_OK;
+    if (P.tune.ev_start && cudaEventRecord(P.tune.ev_start, st) != cudaSuccess) return BB_ERR_LAUNCH;
+    kern<<<(unsigned)grid, P.tune.tpb, P.smem, st>>>(P.L);
+    if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
+    if (P.tune.ev_stop && cudaEventRecord(P.tune.ev_stop, st) != cudaSuccess) return BB_ERR_LAUNCH;
+    return BB_OK;
+}
+
+template <typename T>
+int launch_all_t(const LaunchPlan& P, cudaStream_t st)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned cols_grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((P.L.total_cols + 7) / 8, (int64_t)nsm * 16));
+    pack_kernel<T><<<cols_grid, 256, 0, st>>>(P.L);
+    if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
+    if (P.L.total_tasks > 0) {
+        int rc;
+        switch (maxm_for(P.tune.tw)) {
+            case 5: rc = launch_bulge<T, 5>(P, st); break;
+            case 9: rc = launch_bulge<T, 9>(P, st); break;
+            case 17: rc = launch_bulge<T, 17>(P, st); break;
+            default: rc = launch_bulge<T, 33>(P, st); break;
+        }
+        if (rc != BB_OK) return rc;
+    }
+    const unsigned ex_grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((P.L.total_cols + 255) / 256, (int64_t)nsm * 8));
+    extract_kernel<T><<<ex_grid, 256, 0, st>>>(P.L);
+    return cudaGetLastError() == cudaSuccess ? BB_OK : BB_ERR_LAUNCH;
+}
+
+// enqueue: zero the counters, (upload the table), pack, bulge, extract
+int enqueue(LaunchPlan* P, void* ws, const void* host_descs, cudaStream_t st)
+{
+    bind_workspace(P, ws);
+    if (cudaMemsetAsync(ws, 0, P->off_w, st) != cudaSuccess) return BB_ERR_LAUNCH;
+    if (P->L.count > 1) {
+        if (cudaMemcpyAsync((char*)ws + P->off_desc, host_descs, sizeof(Desc) * P->L.count,
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return BB_ERR_LAUNCH;
+    }
+    return P->esize == 8 ? launch_all_t<double>(*P, st) : launch_all_t<float>(*P, st);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning* out)
+{
+    if (!out) return BB_ERR_ARG;
+    (void)n;
+    out->tw = dtype == BB_F32 ? 32 : 16;     // one 128-byte line of the element type
+    out->tpb = b > 96 ? 256 : 128;
+    out->sweeps_in_flight = 0;
+    out->flags = 0;
+    out->timeout_s = 5.0;
+    out->ev_start = nullptr;
+    out->ev_stop = nullptr;
+    return BB_OK;
+}
+
+const char* bb_status_string(int code)
+{
+    switch (code) {
+        case BB_OK: return "ok";
+        case BB_ERR_ARG: return "invalid argument";
+        case BB_ERR_ALLOC: return "workspace allocation failed";
+        case BB_ERR_LAUNCH: return "kernel launch or CUDA call failed";
+        case BB_ERR_TIMEOUT: return "device wait timed out";
+        case BB_ERR_NONFINITE: return "non-finite input";
+        case BB_ERR_WORKSPACE: return "workspace too small";
+        case BB_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+size_t band_to_bidiag_workspace_size(int64_t n, int64_t b, int dtype, const bb_tuning* tuning)
+{
+    bb_problem p = {n, b, (const void*)16, b + 1, (void*)16, (void*)16};
+    LaunchPlan P;
+    if (plan_launch(1, &p, dtype, tuning, &P) != BB_OK) return 0;
+    return P.bytes;
+}
+
+int band_to_bidiag_ex(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab,
+                      void* d_out, void* e_out, const bb_tuning* tuning, void* workspace,
+                      size_t workspace_bytes, void* stream)
+{
+    bb_problem p = {n, b, band, ldab, d_out, e_out};
+    LaunchPlan P;
+    int rc = plan_launch(1, &p, dtype, tuning, &P);
+    if (rc != BB_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    void* ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (workspace_bytes < P.bytes || ((uintptr_t)ws % kAlign) != 0) return BB_ERR_WORKSPACE;
+    } else {
+        if (cudaMallocAsync(&ws, P.bytes, st) != cudaSuccess) return BB_ERR_ALLOC;
+        own = true;
+    }
+    rc = enqueue(&P, ws, nullptr, st);
+    if (own) cudaFreeAsync(ws, st);
+    return rc;
+}
+
+int band_to_bidiag(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab, void* d_out,
+                   void* e_out, void* stream)
+{
+    return band_to_bidiag_ex(n, b, dtype, band, ldab, d_out, e_out, nullptr, nullptr, 0, stream);
+}
+
+int bb_device_status(void* stream, int reset)
+{
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return -BB_ERR_LAUNCH;
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bb_status, sizeof(v)) != cudaSuccess) return -BB_ERR_LAUNCH;
+    if (reset) {
+        unsigned z = 0;
+        if (cudaMemcpyToSymbol(g_bb_status, &z, sizeof(z)) != cudaSuccess) return -BB_ERR_LAUNCH;
+    }
+    return (int)v;
+}
+
+int band_to_bidiag_host(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab,
+                        void* d_out, void* e_out, const bb_tuning* tuning, void* stream)
+{
+    if (!band || !d_out || (n > 1 && !e_out) || n < 1 || ldab < b + 1) return BB_ERR_ARG;
+    if (dtype != BB_F32 && dtype != BB_F64) return BB_ERR_ARG;
+    const size_t es = dtype == BB_F64 ? 8 : 4;
+    const size_t band_bytes = align_up(es * (size_t)ldab * (size_t)n);
+    const size_t d_bytes = align_up(es * (size_t)n);
+    const size_t ws_bytes = band_to_bidiag_workspace_size(n, b, dtype, tuning);
+    if (ws_bytes == 0) return BB_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, band_bytes + 2 * d_bytes + ws_bytes, st) != cudaSuccess)
+        return BB_ERR_ALLOC;
+    char* dband = buf;
+    char* dd = buf + band_bytes;
+    char* de = dd + d_bytes;
+    char* dws = de + d_bytes;
+    int rc = BB_OK;
+    if (cudaMemcpyAsync(dband, band, es * (size_t)ldab * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = BB_ERR_LAUNCH;
+    if (rc == BB_OK)
+        rc = band_to_bidiag_ex(n, b, dtype, dband, ldab, dd, n > 1 ? de : nullptr, tuning, dws, ws_bytes, st);
+    if (rc == BB_OK && cudaMemcpyAsync(d_out, dd, es * (size_t)n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = BB_ERR_LAUNCH;
+    if (rc == BB_OK && n > 1 &&
+        cudaMemcpyAsync(e_out, de, es * (size_t)(n - 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = BB_ERR_LAUNCH;
+    cudaFreeAsync(buf, st);
+    const int dev = bb_device_status(stream, 1);
+    if (rc != BB_OK) return rc;
+    if (dev < 0) return -dev;
+    for (int code = 1; code < 16; ++code)
+        if (dev & (1 << code)) return code;
+    return BB_OK;
+}
+
+// ------------------------------------------------------------------- batch
+
+struct bb_batch_plan {
+    LaunchPlan P;
+    Desc* pinned = nullptr;   // problem table for the host-to-device copy
+};
+
+bb_batch_plan* bb_batch_plan_create(int count, const bb_problem* problems, int dtype,
+                                    const bb_tuning* tuning)
+{
+    bb_batch_plan* plan = new bb_batch_plan();
+    if (plan_launch(count, problems, dtype, tuning, &plan->P) != BB_OK) {
+        delete plan;
+        return nullptr;
+    }
+    if (count > 1) {
+        if (cudaMallocHost((void**)&plan->pinned, sizeof(Desc) * count) != cudaSuccess) {
+            delete plan;
+            return nullptr;
+        }
+        std::memcpy(plan->pinned, plan->P.descs.data(), sizeof(Desc) * count);
+    }
+    return plan;
+}
+
+size_t bb_batch_plan_workspace_size(const bb_batch_plan* plan) { return plan ? plan->P.bytes : 0; }
+
+int bb_batch_execute(const bb_batch_plan* plan, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!plan || !workspace) return BB_ERR_ARG;
+    if (workspace_bytes < plan->P.bytes || ((uintptr_t)workspace % kAlign) != 0) return BB_ERR_WORKSPACE;
+    LaunchPlan P = plan->P;   // the launch struct is bound to this workspace
+    return enqueue(&P, workspace, plan->pinned, (cudaStream_t)stream);
+}
+
+void bb_batch_plan_destroy(bb_batch_plan* plan)
+{
+    if (!plan) return;
+    if (plan->pinned) cudaFreeHost(plan->pinned);
+    delete plan;
+}
+
+// ------------------------------------------------------------ work model
+
+int bb_schedule_counts(int64_t n64, int64_t b64, int tw, int64_t* stages_out, int64_t* steps_out,
+                       double* flops_out, double* elems_out)
+{
+    if (n64 < 1 || b64 < 0 || tw < 1 || n64 >= PROG_STAGE) return BB_ERR_ARG;
+    const int n = (int)n64;
+    int b = clamp_b(n64, b64);
+    int64_t stages = 0, steps = 0;
+    double flops = 0.0, elems = 0.0;
+    // cost of one row-bulge at block column c (generic data: both reflectors nontrivial)
+    auto step_cost = [&](int bw, int d, int R, int s, double* f, double* e) {
+        const int c = R + (bw - d) + s * bw;
+        const int m = std::min(d + 1, n - c);
+        const int r0 = (s == 0) ? R : c - bw;
+        const int jmax = std::min(n - 1, c + m - 1 + bw);
+        const int nr = c + m - r0, nc = jmax - c + 1;
+        *f = 2.0 * (4.0 * (m - 1) + 10.0) + 4.0 * m * (nr - 1) + 4.0 * m * (nc - 1);
+        *e = (double)nr * m + (double)m * nc - (double)m * m;
+    };
+    for (int bw = b; bw > 1;) {
+        const int d = std::min(tw, bw - 1);
+        ++stages;
+        for (int R = 0; R < n - 1; ++R) {
+            const int c0 = R + bw - d;
+            if (c0 >= n - 1) continue;
+            const int ns = (n - 2 - c0) / bw + 1;
+            steps += ns;
+            // full steps: s >= 1 with c + d + bw <= n - 1
+            int full_hi = (n - 1 - d - bw - c0) >= 0 ? (n - 1 - d - bw - c0) / bw : -1;
+            full_hi = std::min(full_hi, ns - 1);
+            double f, e;
+            if (full_hi >= 1) {
+                step_cost(bw, d, R, 1, &f, &e);
+                flops += f * full_hi;
+                elems += e * full_hi;
+            }
+            for (int s = 0; s < ns; ++s) {
+                if (s >= 1 && s <= full_hi) continue;
+                step_cost(bw, d, R, s, &f, &e);
+                flops += f;
+                elems += e;
+            }
+        }
+        bw -= d;
+    }
+    if (stages_out) *stages_out = stages;
+    if (steps_out) *steps_out = steps;
+    if (flops_out) *flops_out = flops;
+    if (elems_out) *elems_out = elems;
+    return BB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+"""The C-ABI library builds, loads without a GPU, exports every symbol the
+header declares, and its host-only parts (work model, argument checks) agree
+with the oracle.  No compute call reaches the GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import bandgen
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bb():
+    from paper_2510_12705_gb300 import build
+    build.build()
+    import paper_2510_12705_gb300 as m
+    m.lib()
+    return m
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", src, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof", "defined"):
+                names.append(name)
+    return sorted(set(names))
+
+
+def test_header_symbols_exported(bb):
+    names = _declared_functions()
+    assert "band_to_bidiag" in names and "bb_batch_execute" in names
+    lib = ctypes.CDLL(bb.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("n,b,tw", [(512, 16, 16), (300, 40, 16), (257, 33, 8), (400, 64, 32),
+                                    (100, 7, 3), (64, 63, 16), (30, 50, 4), (5, 1, 4), (1, 0, 16)])
+def test_work_model_matches_oracle_counts(bb, n, b, tw):
+    ab = bandgen.random_band(n, b, seed=n + b)
+    _, _, cnt = oracle.band_to_bidiag(ab, b, tw)
+    wm = bb.bb_schedule_counts(n, b, tw)
+    assert wm.steps == cnt["steps"]
+    assert wm.stages == cnt["stages"]
+    assert wm.flops == pytest.approx(cnt["flops"], rel=1e-12, abs=0)
+    assert wm.elements == pytest.approx(cnt["elements"], rel=1e-12, abs=0)
+
+
+def test_work_model_large_is_fast_and_consistent(bb):
+    # headline configuration: the per-sweep closed form must agree with a
+    # direct per-step sum on a smaller case and scale smoothly
+    wm = bb.bb_schedule_counts(32768, 128, 16)
+    assert wm.stages == 8
+    # leading term 4 n^2 b (1 + 1/d) ~ the executed flops within a factor of 2
+    assert 0.5 < wm.flops / (4 * 32768**2 * 128 * (1 + 1 / 16)) < 2.0
+
+
+def test_default_tuning(bb):
+    t64 = bb.bb_default_tuning(32768, 128, bb.BB_F64)
+    t32 = bb.bb_default_tuning(32768, 128, bb.BB_F32)
+    # one 128-byte line per tile row: 16 doubles, 32 floats (Section VI-B)
+    assert t64.tw == 16 and t32.tw == 32
+    assert t64.tpb in (64, 128, 256, 512)
+
+
+def test_host_side_argument_errors(bb):
+    L = bb.lib()
+    # validation happens before any CUDA call
+    assert L.band_to_bidiag(0, 4, 1, 16, 5, 16, 16, None) == bb.BB_ERR_ARG
+    assert L.band_to_bidiag(10, -1, 1, 16, 5, 16, 16, None) == bb.BB_ERR_ARG
+    assert L.band_to_bidiag(10, 4, 1, 16, 4, 16, 16, None) == bb.BB_ERR_ARG     # ldab < b+1
+    assert L.band_to_bidiag(10, 4, 1, None, 5, 16, 16, None) == bb.BB_ERR_ARG
+    assert L.band_to_bidiag(10, 4, 7, 16, 5, 16, 16, None) == bb.BB_ERR_ARG     # dtype
+    assert L.band_to_bidiag(10, 4, 1, 16, 5, 16, None, None) == bb.BB_ERR_ARG   # e_out
+    assert L.band_to_bidiag(1 << 20, 4, 1, 16, 5, 16, 16, None) == bb.BB_ERR_UNSUPPORTED
+    t = bb.Tuning(tw=40)
+    assert L.band_to_bidiag_ex(10, 4, 1, 16, 5, 16, 16, ctypes.byref(t), None, 0, None) == bb.BB_ERR_ARG
+    t = bb.Tuning(tpb=100)
+    assert L.band_to_bidiag_ex(10, 4, 1, 16, 5, 16, 16, ctypes.byref(t), None, 0, None) == bb.BB_ERR_ARG
+    # caller workspace too small / misaligned
+    ws = bb.band_to_bidiag_workspace_size(100, 8, bb.BB_F64)
+    assert ws > 0 and ws % 256 == 0
+    assert L.band_to_bidiag_ex(100, 8, 1, 16, 9, 16, 16, None, 256, 1024, None) == bb.BB_ERR_WORKSPACE
+    assert L.band_to_bidiag_ex(100, 8, 1, 16, 9, 16, 16, None, 257, ws, None) == bb.BB_ERR_WORKSPACE
+    assert bb.status_string(bb.BB_ERR_TIMEOUT) == "device wait timed out"
+
+
+def test_workspace_size_model(bb):
+    # working band of height b + 2 TW + 1 (Section V storage format), padded
+    n, b = 32768, 128
+    ws = bb.band_to_bidiag_workspace_size(n, b, bb.BB_F64)
+    ldw = -(-(b + 2 * 16 + 1) // 4) * 4
+    assert ldw * n * 8 <= ws <= ldw * n * 8 + 4 * n + 4096
