@@ -177,6 +177,28 @@ int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning *out);
 double bb_measure_l2_bandwidth(size_t bytes, int reps, void *stream);
 double bb_measure_fma_peak(int dtype, void *stream);
 
+/*
+ * band_to_bidiag_noalloc -- the paper has no counterpart; this is a library
+ * convenience.  Same contract as band_to_bidiag (default tuning), but the call
+ * allocates no device memory: its scratch is a statically sized device array
+ * defined by this library, for callers that cannot allocate at call time
+ * (inside a CUDA stream capture that must stay free of allocation nodes, under
+ * an external allocator that owns all device memory, or from host code with no
+ * allocation facility).  Limits:
+ *   - every GPU that loads the library keeps band_to_bidiag_noalloc_max_bytes()
+ *     (16 MiB) reserved until process exit;
+ *   - a problem whose workspace (band_to_bidiag_workspace_size with default
+ *     tuning) exceeds that size is rejected with BB_ERR_WORKSPACE before any
+ *     GPU work;
+ *   - all calls on a device share the array: calls whose GPU work may overlap
+ *     race and corrupt each other; issue them on one stream;
+ *   - the first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ */
+int band_to_bidiag_noalloc(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab,
+                           void *d_out, void *e_out, void *stream);
+size_t band_to_bidiag_noalloc_max_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

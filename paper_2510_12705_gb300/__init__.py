@@ -272,3 +272,21 @@ class BatchPlan:
         if p and _lib is not None:
             _lib.bb_batch_plan_destroy(p)
             self._plan = None
+
+
+def band_to_bidiag_noalloc(band, b: int, d_out, e_out, stream=None) -> None:
+    """Allocation-free reduction: like band_to_bidiag, but the library's fixed
+    16 MiB device scratch array is used instead of any allocation.  For callers
+    that cannot allocate device memory at call time (stream capture without
+    allocation nodes, an external allocator owning all memory).  Calls that may
+    overlap on the GPU share that array and race; keep them on one stream.
+    Raises BBError(BB_ERR_WORKSPACE) when the problem does not fit."""
+    L = lib()
+    f = L.band_to_bidiag_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    n, ldab = _check_band(band, d_out, e_out)
+    rc = f(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab, d_out.data_ptr(),
+           e_out.data_ptr() if n > 1 else None, _stream_handle(stream))
+    _check(rc, "band_to_bidiag_noalloc")

@@ -665,3 +665,64 @@ int bb_schedule_counts(int64_t n64, int64_t b64, int tw, int64_t* stages_out, in
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- allocation-free variant
+//
+// Some callers cannot allocate device memory at the point where they need the
+// reduction: code running inside a CUDA stream capture that must not add
+// allocation nodes, callers whose memory is fully reserved up front by their
+// own pool or another framework's caching allocator, or host environments
+// with no way to obtain or free a workspace.  band_to_bidiag_noalloc serves
+// them: its scratch (counters and the working band) lives in one statically
+// sized device array that the library defines, so the call allocates nothing.
+//
+// Cost and limits: every GPU that loads this library keeps the array
+// (kNoAllocScratchBytes = 16 MiB) reserved until the process exits.  Problems
+// whose workspace exceeds it are rejected.  All calls on a device share the one
+// array, so calls whose GPU work may overlap (different streams, or
+// concurrent host threads) race and corrupt each other's results; serialise
+// them on one stream.  The counters at the front of the array are cleared on
+// the stream by every call.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 16u << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device (set up once per
+// device, with that device current).  The host-side symbol is only a stand-in
+// for the device array and must never be handed to a kernel.
+void* noalloc_scratch_for_current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" size_t band_to_bidiag_noalloc_max_bytes(void) { return kNoAllocScratchBytes; }
+
+extern "C" int band_to_bidiag_noalloc(int64_t n, int64_t b, int dtype, const void* band,
+                                      int64_t ldab, void* d_out, void* e_out, void* stream)
+{
+    bb_problem p = {n, b, band, ldab, d_out, e_out};
+    LaunchPlan P;
+    int rc = plan_launch(1, &p, dtype, nullptr, &P);
+    if (rc != BB_OK) return rc;
+    if (P.bytes > kNoAllocScratchBytes) return BB_ERR_WORKSPACE;
+    void* ws = noalloc_scratch_for_current_device();
+    if (!ws) return BB_ERR_LAUNCH;
+    return enqueue(&P, ws, nullptr, (cudaStream_t)stream);
+}
