@@ -77,124 +77,264 @@ __global__ void extract_kernel(Launch L)
     }
 }
 
-// One row-bulge (Algorithm 2) of sweep R, stage (bw, d), on the CTA.
-template <typename T, int MAXM>
-__device__ __forceinline__ void row_bulge(const Desc& D, T* __restrict__ W, int bw, int d, int R,
-                                          int s, T* RP, int rpn, T* LP, T* vR, T* vL, T* tb)
+// ------------------------------------------------------------- row-bulge
+// Shared-memory panels (odd pitch MAXM: conflict-free, compile-time offsets):
+//   RP  right panel, row-major: panel row ri (matrix row r0+ri), column k at
+//       RP[ri*MAXM + k]
+//   LP  left panel, column-major: column jj (matrix column c+jj), row k
+//       (matrix row c+k) at LP[jj*MAXM + k]
+// Warp 0 computes each reflector; the other warps ("workers") own the rows and
+// columns, two threads per row / column (thread p in {0,1} of a pair holds
+// entries [p*H, p*H+H); one shuffle combines their partial dot products).
+template <int MAXM> struct Split { static constexpr int H = (MAXM + 1) / 2; };
+
+__device__ __forceinline__ void bar_arrive(int id, int n)
 {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_sync_n(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// e / div for 0 <= e < 2^22, div >= 1, via an FP32 reciprocal plus correction
+__device__ __forceinline__ int fast_div(int e, int div, float inv)
+{
+    int q = (int)((float)e * inv);
+    int r = e - q * div;
+    if (r < 0) --q;
+    else if (r >= div) ++q;
+    return q;
+}
+
+// left-panel columns jj in [lo, hi) back to the working band (exact rows)
+template <typename T, int MAXM>
+__device__ __forceinline__ void left_store(const T* LP, T* __restrict__ W, int ldw, int top, int c,
+                                           int m, int lo, int hi)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int jj = lo + warp; jj < hi; jj += nw) {
+        T* col = W + (int64_t)(c + jj) * ldw + (top - jj);
+        if (lane < m) stcg(col + lane, LP[jj * MAXM + lane]);
+        if (MAXM > 32 && lane + 32 < m) stcg(col + lane + 32, LP[jj * MAXM + lane + 32]);
+    }
+}
+
+// One row-bulge (Algorithm 2) of sweep R, stage (bw, d), on the CTA.
+//
+// A: every thread issues its share of the panel loads (right panel rows
+//    r0..c+m-1 x columns c..c+m-1 -> RP; left panel columns c+m.. before the
+//    tail, rows c..c+m-1 -> LP), U loads in flight per batch.
+// B: warp 0 scales row r0 and builds the right reflector; meanwhile, as soon
+//    as the scaled row is published (named barrier), the workers form the
+//    dot products of the other rows with it: row.v = row_0 + vs * sum_k>0
+//    row_k t_k.  C: workers update the rows; rows above c go back to the
+//    working band, rows c..c+m-1 (shared with the left panel) into LP.
+// D/E: the same for the left reflector (column c) and the left panel's
+//    columns, which are then stored one warp per column.
+// The left panel's tail columns (offset >= tail_start) are the only part the
+// previous sweep's next row-bulge also writes: they are loaded after the wait
+// on it (tail_prog >= tail_target) and updated straight from registers.
+// Returns false when a wait gave up.
+template <typename T, int MAXM>
+__device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int bw, int d, int R,
+                                          int s, T* RP, T* LP, T* wbuf, T* tsR, T* tsL, T* vR, T* vL,
+                                          T* tb, int* s_flag, const int* tail_prog, int tail_target,
+                                          int tail_start, Header* hdr, unsigned long long timeout_ns)
+{
+    constexpr int H = Split<MAXM>::H;
     const int n = D.n, ldw = D.ldw, top = D.top;
     const int c = R + (bw - d) + s * bw;
     const int m = min(d + 1, n - c);
     const int r0 = (s == 0) ? R : c - bw;
-    const int nr = c + m - r0;                 // rows r0 .. c+m-1
+    const int nr = c + m - r0;                 // panel rows r0 .. c+m-1 (panel row 0 = r0)
     const int jmax = min(n - 1, c + m - 1 + bw);
-    const int nc = jmax - c + 1;               // columns c .. jmax
-    const int ro = c - r0;                     // right-panel row of matrix row c
+    const int ncols = jmax - c;                // columns c+1 .. jmax (offset jj = 1..ncols)
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wt = tid - 32, nwt = nt - 32;    // worker index / count (warps 1..)
+    const int p = tid & 1, k0 = p * H;
+    const int pre_hi = min(tail_start, ncols + 1);   // left-panel columns loaded up front
 
-    // stage the right panel (column-major, rows fastest) ...
-    for (int f = tid; f < nr * m; f += nt) {
-        const int k = f / nr, r = f - k * nr;
-        RP[k * rpn + r] = ldcg(W + (int64_t)(c + k) * ldw + (r0 - c - k + top + r));
-    }
-    // ... and the left panel's columns right of the overlap block
-    for (int f = tid; f < (nc - m) * m; f += nt) {
-        const int jj = m + f / m, k = f - (jj - m) * m;
-        LP[jj * MAXM + k] = ldcg(W + (int64_t)(c + jj) * ldw + (top - jj + k));
-    }
-    __syncthreads();
-
-    // right reflector from row r0, applied to rows r0+1 .. c+m-1
-    if (tid < 32) warp_reflector<T>(m, RP, rpn, vR, tb);
-    __syncthreads();
+    // ---- A: loads
     {
-        const T tau = tb[0];
-        for (int r = 1 + tid; r < nr; r += nt) {
-            T a[MAXM];
-            T w = (T)0;
+        constexpr int U = sizeof(T) == 8 ? 8 : 12;
+        const int totR = nr * m, totL = (pre_hi - m) * m, tot = totR + totL;
+        const float invR = 1.0f / (float)nr, invM = 1.0f / (float)m;
+        for (int base = tid; base < tot; base += U * nt) {
+            T val[U];
+            int dst[U];
 #pragma unroll
-            for (int k = 0; k < MAXM; ++k)
-                if (k < m) { a[k] = RP[k * rpn + r]; w = fma(a[k], vR[k], w); }
-            w *= tau;
+            for (int u = 0; u < U; ++u) {
+                const int e = base + u * nt;
+                dst[u] = -1;
+                if (e < totR) {
+                    const int k = fast_div(e, nr, invR), ri = e - k * nr;
+                    val[u] = ldcg(W + (int64_t)(c + k) * ldw + (r0 + ri - c - k + top));
+                    dst[u] = ri * MAXM + k;
+                } else if (e < tot) {
+                    const int f = e - totR;
+                    const int q = fast_div(f, m, invM), k = f - q * m, jj = m + q;
+                    val[u] = ldcg(W + (int64_t)(c + jj) * ldw + (top - jj + k));
+                    dst[u] = -2 - (jj * MAXM + k);
+                }
+            }
 #pragma unroll
-            for (int k = 0; k < MAXM; ++k)
-                if (k < m) RP[k * rpn + r] = fma(-w, vR[k], a[k]);
+            for (int u = 0; u < U; ++u) {
+                if (dst[u] >= 0) RP[dst[u]] = val[u];
+                else if (dst[u] <= -2) LP[-2 - dst[u]] = val[u];
+            }
         }
-        if (tid < m) RP[tid * rpn] = (tid == 0) ? tb[1] : (T)0;
     }
     __syncthreads();
 
-    // overlap block (rows c.., columns c..c+m-1) after the right reflector
-    for (int f = tid; f < m * m; f += nt) {
-        const int kc = f / m, k = f - kc * m;
-        LP[kc * MAXM + k] = RP[kc * rpn + ro + k];
-    }
-    __syncthreads();
-
-    // left reflector from column c, applied to columns c+1 .. jmax
-    if (tid < 32) warp_reflector<T>(m, LP, 1, vL, tb + 2);
-    __syncthreads();
-    {
-        const T tau = tb[2];
-        for (int jj = 1 + tid; jj < nc; jj += nt) {
-            T a[MAXM];
+    // ---- B: right reflector (warp 0) || row dot products (workers)
+    if (warp == 0) {
+        const ReflScale sc = reflector_scale<T>(m, RP, tsR);
+        bar_arrive(1, nt);
+        reflector_finish<T>(m, sc, vR, tb);
+    } else {
+        bar_sync_n(1, nt);
+        for (int ri = 1 + (wt >> 1); ri - (wt >> 1) < nr; ri += nwt >> 1) {
             T w = (T)0;
+            if (ri < nr) {
+                const T* row = RP + ri * MAXM + k0;
 #pragma unroll
-            for (int k = 0; k < MAXM; ++k)
-                if (k < m) { a[k] = LP[jj * MAXM + k]; w = fma(vL[k], a[k], w); }
-            w *= tau;
-#pragma unroll
-            for (int k = 0; k < MAXM; ++k)
-                if (k < m) LP[jj * MAXM + k] = fma(-w, vL[k], a[k]);
+                for (int i = 0; i < H; ++i)
+                    if (k0 + i >= 1 && k0 + i < m) w = fma(row[i], tsR[k0 + i], w);
+            }
+            w += __shfl_xor_sync(FULL, w, 1);
+            if (ri < nr && p == 0) wbuf[ri] = w;
         }
-        if (tid < m) LP[tid] = (tid == 0) ? tb[3] : (T)0;
     }
     __syncthreads();
 
-    // write back: right panel rows r0 .. c-1, then the whole left panel
-    for (int f = tid; f < ro * m; f += nt) {
-        const int k = f / ro, r = f - k * ro;
-        stcg(W + (int64_t)(c + k) * ldw + (r0 - c - k + top + r), RP[k * rpn + r]);
+    // ---- C: row updates
+    if (warp == 0) {
+        for (int k = lane; k < m; k += 32)
+            stcg(W + (int64_t)(c + k) * ldw + (r0 - c - k + top), k == 0 ? tb[1] : (T)0);
+    } else {
+        const T tau = tb[0], vs = tb[2];
+        for (int ri = 1 + (wt >> 1); ri < nr; ri += nwt >> 1) {
+            const int r = r0 + ri;
+            const T* row = RP + ri * MAXM + k0;
+            const T u = tau * fma(vs, wbuf[ri], RP[ri * MAXM]);
+            if (r >= c) {          // shared block: left-panel column k, row r - c
+#pragma unroll
+                for (int i = 0; i < H; ++i)
+                    if (k0 + i < m) LP[(k0 + i) * MAXM + (r - c)] = fma(-u, vR[k0 + i], row[i]);
+            } else {
+                T* dst = W + (int64_t)(c + k0) * ldw + (r - c - k0 + top);   // (r, c+k0)
+#pragma unroll
+                for (int i = 0; i < H; ++i)
+                    if (k0 + i < m) stcg(dst + (int64_t)i * (ldw - 1), fma(-u, vR[k0 + i], row[i]));
+            }
+        }
     }
-    for (int f = tid; f < nc * m; f += nt) {
-        const int jj = f / m, k = f - jj * m;
-        stcg(W + (int64_t)(c + jj) * ldw + (top - jj + k), LP[jj * MAXM + k]);
+    __syncthreads();
+
+    // ---- D: left reflector (warp 0) || column dot products (workers)
+    T* tbL = tb + 4;
+    if (warp == 0) {
+        const ReflScale sc = reflector_scale<T>(m, LP, tsL);
+        bar_arrive(1, nt);
+        reflector_finish<T>(m, sc, vL, tbL);
+    } else {
+        bar_sync_n(1, nt);
+        for (int jj = 1 + (wt >> 1); jj - (wt >> 1) < pre_hi; jj += nwt >> 1) {
+            T w = (T)0;
+            if (jj < pre_hi) {
+                const T* col = LP + jj * MAXM + k0;
+#pragma unroll
+                for (int i = 0; i < H; ++i)
+                    if (k0 + i >= 1 && k0 + i < m) w = fma(col[i], tsL[k0 + i], w);
+            }
+            w += __shfl_xor_sync(FULL, w, 1);
+            if (jj < pre_hi && p == 0) wbuf[jj] = w;
+        }
     }
+    __syncthreads();
+
+    // ---- E: column updates in LP, then coalesced stores
+    const T tauL = tbL[0], vsL = tbL[2];
+    if (warp == 0) {
+        for (int k = lane; k < m; k += 32) LP[k] = k == 0 ? tbL[1] : (T)0;
+    } else {
+        for (int jj = 1 + (wt >> 1); jj < pre_hi; jj += nwt >> 1) {
+            T* col = LP + jj * MAXM + k0;
+            const T u = tauL * fma(vsL, wbuf[jj], LP[jj * MAXM]);
+#pragma unroll
+            for (int i = 0; i < H; ++i)
+                if (k0 + i < m) col[i] = fma(-u, vL[k0 + i], col[i]);
+        }
+    }
+    __syncthreads();
+    left_store<T, MAXM>(LP, W, ldw, top, c, m, 0, pre_hi);
+
+    // ---- tail: after the previous sweep's next row-bulge, straight from registers
+    if (pre_hi <= ncols) {
+        if (tid == 0) *s_flag = tail_prog ? (int)wait_at_least(tail_prog, tail_target, hdr, timeout_ns) : 1;
+        __syncthreads();
+        if (!*s_flag) return false;
+        if (warp != 0) {
+            for (int jj = pre_hi + (wt >> 1); jj - (wt >> 1) <= ncols; jj += nwt >> 1) {
+                const bool act = jj <= ncols;
+                T* col = W + (int64_t)(c + jj) * ldw + (top - jj) + k0;   // row c+k0 of column c+jj
+                T a[H];
+                T w = (T)0;
+#pragma unroll
+                for (int i = 0; i < H; ++i)
+                    if (act && k0 + i < m) {
+                        a[i] = ldcg(col + i);
+                        if (k0 + i >= 1) w = fma(a[i], tsL[k0 + i], w);
+                    }
+                w += __shfl_xor_sync(FULL, w, 1);
+                const T a0 = __shfl_sync(FULL, act ? a[0] : (T)0, lane & ~1);   // row c (p = 0's first)
+                const T u = tauL * fma(vsL, w, a0);
+#pragma unroll
+                for (int i = 0; i < H; ++i)
+                    if (act && k0 + i < m) stcg(col + i, fma(-u, vL[k0 + i], a[i]));
+            }
+        }
+    }
+    return true;
 }
 
+// One bandwidth-reduction stage (Algorithm 1, all sweeps) of every problem:
+// a persistent launch in which CTAs claim sweeps in order.  Sweep R may start
+// row-bulge s once sweep R-1 has finished row-bulge s (s+2 when the stage
+// ends at bandwidth 1), and its left panel's tail waits for row-bulge s+1 of
+// sweep R-1 (Section III-A separation of 2, resp. 3, row-bulges).
 template <typename T, int MAXM>
 __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* RP = (T*)smem_raw;
-    T* LP = RP + (size_t)MAXM * L.rp_rows;
-    T* vR = LP + (size_t)L.lp_cols * MAXM;
-    T* vL = vR + 64;
-    T* tb = vL + 64;
+    T* RP = (T*)smem_raw;                                  // right panel, L.rp_rows rows
+    T* LP = RP + (size_t)MAXM * L.rp_rows;                 // left panel, L.lp_cols columns
+    T* wbuf = LP + (size_t)MAXM * L.lp_cols;               // per row / column dot products
+    __shared__ T vR[64], vL[64], tsR[64], tsL[64], tb[8];
     __shared__ int s_task[4];
     __shared__ int s_ok;         // result of the per-step wait
-    __shared__ int s_stage_ok;   // result of the stage-barrier wait
+    __shared__ int s_tail_ok;    // result of the tail wait inside a row-bulge
     const int tid = threadIdx.x;
+    const int stage = L.stage;
 
     for (;;) {
         if (tid == 0) {
             int t = -1;
             if (!ld_relaxed(&L.hdr->abort)) t = atomicAdd(&L.hdr->claim, 1);
-            if (t >= 0 && t < L.total_tasks) {
-                const int64_t stage = t / L.sweeps_per_stage;
-                const int64_t r = t - stage * L.sweeps_per_stage;
-                const int q = find_problem_by_sweep(L, r);
-                s_task[0] = (int)stage;
-                s_task[1] = q;
-                s_task[2] = (int)(r - desc_of(L, q).sweep_prefix);
+            if (t >= 0 && t < L.sweeps_per_stage) {
+                const int q = find_problem_by_sweep(L, t);
+                s_task[0] = q;
+                s_task[1] = (int)(t - desc_of(L, q).sweep_prefix);
             } else {
                 s_task[0] = -1;
             }
         }
         __syncthreads();
-        const int stage = s_task[0];
-        if (stage < 0) break;
-        const int q = s_task[1], R = s_task[2];
+        const int q = s_task[0];
+        if (q < 0) break;
+        const int R = s_task[1];
         const Desc& D = desc_of(L, q);
         __syncthreads();   // s_task may be rewritten on the next claim
         if (stage >= D.nstages) continue;
@@ -202,44 +342,36 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         const int n = D.n;
         const int bw = stage_bw(D.b, L.tw, stage);
         const int d = stage_d(bw, L.tw);
-        const int lag = (bw - d >= 2) ? 2 : 3;
+        const bool split = (bw - d) >= 2;
         const int base = stage * PROG_STAGE;
         int* prog = L.prog + D.prog_off;
+        const int ps = L.prog_stride;
         const int ns = sweep_steps(n, bw, d, R);
         const int nsp = (R > 0) ? sweep_steps(n, bw, d, R - 1) : 0;
         T* W = (T*)L.wbase + D.w_off;
         const bool stall = (L.flags & BB_FLAG_INJECT_STALL) && stage == 0 && R == 0;
 
-        if (tid == 0) {
-            bool ok = true;
-            if (stage > 0) ok = wait_at_least(&L.stage_done[q], stage * (n - 1), L.hdr, L.timeout_ns);
-            s_stage_ok = ok;
-        }
-        __syncthreads();
-        if (!s_stage_ok) break;
-
         bool ok = true;
         for (int s = 0; s < ns; ++s) {
             if (tid == 0) {
                 bool w_ok = true;
-                if (R > 0) w_ok = wait_at_least(&prog[R - 1], base + min(s + lag, nsp), L.hdr, L.timeout_ns);
+                if (R > 0)
+                    w_ok = wait_at_least(&prog[(R - 1) * ps], base + min(s + (split ? 1 : 3), nsp),
+                                         L.hdr, L.timeout_ns);
                 s_ok = w_ok;
             }
             __syncthreads();
             if (!s_ok) { ok = false; break; }
-            row_bulge<T, MAXM>(D, W, bw, d, R, s, RP, L.rp_rows, LP, vR, vL, tb);
+            const bool step_ok = row_bulge<T, MAXM>(
+                D, W, bw, d, R, s, RP, LP, wbuf, tsR, tsL, vR, vL, tb, &s_tail_ok,
+                (split && R > 0) ? &prog[(R - 1) * ps] : nullptr, base + min(s + 2, nsp),
+                split ? bw - 1 : (1 << 30), L.hdr, L.timeout_ns);
             __syncthreads();
-            if (tid == 0 && !stall) {
-                __threadfence();
-                st_release(&prog[R], base + s + 1);
-            }
+            if (!step_ok) { ok = false; break; }
+            if (tid == 0 && !stall) st_release(&prog[R * ps], base + s + 1);   // cumulative release
         }
         if (!ok) break;
-        if (tid == 0 && !stall) {
-            if (ns == 0) st_release(&prog[R], base);
-            __threadfence();
-            atomicAdd(&L.stage_done[q], 1);
-        }
+        if (tid == 0 && !stall && ns == 0) st_release(&prog[R * ps], base);
     }
 }
 
@@ -287,7 +419,7 @@ bool resolve_tuning(int64_t n, int64_t b, int dtype, const bb_tuning* t, Resolve
     r->ev_start = t ? (cudaEvent_t)t->ev_start : nullptr;
     r->ev_stop = t ? (cudaEvent_t)t->ev_stop : nullptr;
     if (r->tw < 1 || r->tw > 32) return false;
-    if (r->tpb != 64 && r->tpb != 128 && r->tpb != 256 && r->tpb != 512) return false;
+    if (r->tpb != 0 && (r->tpb < 64 || r->tpb > 512 || r->tpb % 32 != 0)) return false;
     return true;
 }
 
@@ -331,16 +463,17 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
         D.b_in = (int)p.b;
         D.nstages = num_stages(D.b, tw);
         D.top = D.b + tw;
-        D.ldw = (int)align_up((size_t)(D.b + 2 * tw + 1), 4);
+        D.ldw = (int)align_up((size_t)(D.b + 2 * tw), 4) + 1;   // ldw - 1 multiple of 4
         D.w_off = welems;
-        D.prog_off = col_prefix;
+        D.prog_off = col_prefix * (count == 1 ? 32 : 4);
         D.sweep_prefix = sweep_prefix;
         D.col_prefix = col_prefix;
         D.band = p.band;
         D.ldab = p.ldab;
         D.d = p.d_out;
         D.e = p.e_out;
-        welems += (int64_t)align_up((size_t)D.ldw * (size_t)D.n * P->esize) / P->esize;
+        // + 16 elements: the 16-byte covers of the last columns may read past the band
+        welems += (int64_t)align_up(((size_t)D.ldw * (size_t)D.n + 16) * P->esize) / P->esize;
         sweep_prefix += D.n - 1;
         col_prefix += D.n;
         max_stages = std::max(max_stages, D.nstages);
@@ -351,7 +484,8 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
     size_t off = 0;
     P->off_hdr = off;   off = align_up(off + sizeof(Header));
     P->off_stage = off; off = align_up(off + sizeof(int) * (size_t)count);
-    P->off_prog = off;  off = align_up(off + sizeof(int) * (size_t)col_prefix);
+    const int prog_stride = count == 1 ? 32 : 4;   // a 128-byte line per sweep when alone
+    P->off_prog = off;  off = align_up(off + sizeof(int) * (size_t)col_prefix * prog_stride);
     P->off_desc = off;  off = align_up(off + (count > 1 ? sizeof(Desc) * (size_t)count : 0));
     P->off_w = off;     off = align_up(off + (size_t)welems * P->esize);
     P->bytes = off;
@@ -367,10 +501,11 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
     L.total_cols = col_prefix;
     L.timeout_ns = P->tune.timeout_ns;
     L.flags = P->tune.flags;
-    L.rp_rows = max_b + tw + 1;
-    L.lp_cols = max_b + tw + 1;
-    const int maxm = maxm_for(tw);
-    P->smem = (size_t)P->esize * ((size_t)maxm * L.rp_rows + (size_t)L.lp_cols * maxm + 2 * 64 + 4) + 64;
+    L.prog_stride = prog_stride;
+    L.rp_rows = max_b + tw + 2;
+    L.lp_cols = max_b + tw + 2;
+    L.stage = 0;
+    P->smem = (size_t)P->esize * ((size_t)maxm_for(tw) + 1) * (size_t)(L.rp_rows + L.lp_cols);
     if (L.total_tasks >= (int64_t)INT32_MAX) return BB_ERR_UNSUPPORTED;
     return BB_OK;
 }
@@ -385,27 +520,53 @@ void bind_workspace(LaunchPlan* P, void* ws)
     if (P->L.count > 1) P->L.descs = (const Desc*)(base + P->off_desc);
 }
 
+// threads per bulge for a stage: two per panel row / column
+int stage_tpb(int bw, int d, int user_tpb)
+{
+    if (user_tpb > 0) return user_tpb;
+    int t = 2 * (bw + d + 1);        // two workers per panel row / column
+    t = (t + 31) / 32 * 32 + 32;     // plus the reflector warp
+    return std::max(96, std::min(512, t));
+}
+
 template <typename T, int MAXM>
-int launch_bulge(const LaunchPlan& P, cudaStream_t st)
+int launch_stages(const LaunchPlan& P, cudaStream_t st)
 {
     auto kern = bulge_kernel<T, MAXM>;
     if (P.smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) != cudaSuccess)
             return BB_ERR_UNSUPPORTED;
     }
-    int dev = 0, nsm = 0, per_sm = 0;
+    int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.tune.tpb, P.smem) != cudaSuccess ||
-        per_sm < 1)
-        return BB_ERR_UNSUPPORTED;
-    int64_t grid = (int64_t)nsm * per_sm;
-    if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
-    grid = std::min<int64_t>(grid, P.L.total_tasks);
-    if (grid < 1) return BB_OK;
     if (P.tune.ev_start && cudaEventRecord(P.tune.ev_start, st) != cudaSuccess) return BB_ERR_LAUNCH;
-    kern<<<(unsigned)grid, P.tune.tpb, P.smem, st>>>(P.L);
-    if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
+    Launch L = P.L;
+    for (int stage = 0; stage < P.max_stages; ++stage) {
+        // widest stage-i bandwidth over the problems sizes the CTA
+        int bw_max = 0, d_max = 0;
+        for (const Desc& D : P.descs)
+            if (stage < D.nstages) {
+                const int bw = D.b - stage * L.tw;
+                bw_max = std::max(bw_max, bw);
+                d_max = std::max(d_max, std::min(L.tw, bw - 1));
+            }
+        const int tpb = stage_tpb(bw_max, d_max, P.tune.tpb);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, P.smem) != cudaSuccess ||
+            per_sm < 1)
+            return BB_ERR_UNSUPPORTED;
+        int64_t grid = (int64_t)nsm * per_sm;
+        if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
+        grid = std::min<int64_t>(grid, L.sweeps_per_stage);
+        if (grid < 1) continue;
+        L.stage = stage;
+        // each stage restarts the claim counter (a tiny kernel-free reset)
+        if (stage > 0 && cudaMemsetAsync(&P.L.hdr->claim, 0, sizeof(int), st) != cudaSuccess)
+            return BB_ERR_LAUNCH;
+        kern<<<(unsigned)grid, tpb, P.smem, st>>>(L);
+        if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
+    }
     if (P.tune.ev_stop && cudaEventRecord(P.tune.ev_stop, st) != cudaSuccess) return BB_ERR_LAUNCH;
     return BB_OK;
 }
@@ -420,13 +581,13 @@ int launch_all_t(const LaunchPlan& P, cudaStream_t st)
         1, std::min<int64_t>((P.L.total_cols + 7) / 8, (int64_t)nsm * 16));
     pack_kernel<T><<<cols_grid, 256, 0, st>>>(P.L);
     if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
-    if (P.L.total_tasks > 0) {
+    if (P.max_stages > 0) {
         int rc;
         switch (maxm_for(P.tune.tw)) {
-            case 5: rc = launch_bulge<T, 5>(P, st); break;
-            case 9: rc = launch_bulge<T, 9>(P, st); break;
-            case 17: rc = launch_bulge<T, 17>(P, st); break;
-            default: rc = launch_bulge<T, 33>(P, st); break;
+            case 5: rc = launch_stages<T, 5>(P, st); break;
+            case 9: rc = launch_stages<T, 9>(P, st); break;
+            case 17: rc = launch_stages<T, 17>(P, st); break;
+            default: rc = launch_stages<T, 33>(P, st); break;
         }
         if (rc != BB_OK) return rc;
     }
@@ -460,7 +621,7 @@ int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning* out)
     if (!out) return BB_ERR_ARG;
     (void)n;
     out->tw = dtype == BB_F32 ? 32 : 16;     // one 128-byte line of the element type
-    out->tpb = b > 96 ? 256 : 128;
+    out->tpb = 0;                             // per stage: two threads per panel row / column
     out->sweeps_in_flight = 0;
     out->flags = 0;
     out->timeout_s = 5.0;

@@ -62,7 +62,7 @@ struct Desc {
     int ldw;         // working-band leading dimension
     int top;         // row offset of the diagonal in a working column
     int64_t w_off;   // element offset of the working band in the workspace
-    int64_t prog_off;// int offset of the per-sweep progress words
+    int64_t prog_off;// int offset of the per-sweep progress words (stride prog_stride)
     int64_t sweep_prefix;  // sum of (n - 1) over the previous problems
     int64_t col_prefix;    // sum of n over the previous problems
     const void* band;
@@ -80,13 +80,15 @@ struct Launch {
     int64_t total_tasks;       // max_stages * sweeps_per_stage
     int64_t total_cols;        // sum over problems of n
     void* wbase;          // working bands
-    int* prog;            // progress words
+    int* prog;            // progress words, one per sweep every prog_stride ints
+    int prog_stride;      // 32 (one 128-byte line per sweep) for a single problem
     int* stage_done;      // per problem: completed sweeps over all stages
     Header* hdr;
     unsigned long long timeout_ns;
     int flags;
     int rp_rows;          // shared-memory right panel rows (>= max b + TW + 1)
     int lp_cols;          // shared-memory left panel columns (>= max b + TW + 1)
+    int stage;            // bandwidth-reduction stage of this launch
 };
 
 __device__ __forceinline__ const Desc& desc_of(const Launch& L, int q)
@@ -141,72 +143,145 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 // ------------------------------------------------------ reflector generation
+// Reciprocal and reciprocal square root in FP64 by Newton-Raphson iteration
+// from an FP32 starting value (two steps: ~2^-23 -> ~2^-46 -> full
+// precision).  The argument must be a positive normal number within the FP32
+// range, which the power-of-two scaling in warp_reflector guarantees.
+// STEPS = 1 reaches ~2^-46 (enough for results rounded to FP32), 2 full FP64.
+template <int STEPS>
+__device__ __forceinline__ double newton_rcp(double x)
+{
+    double y = (double)(1.0f / (float)x);
+#pragma unroll
+    for (int i = 0; i < STEPS; ++i) {
+        const double e = fma(-x, y, 1.0);
+        y = fma(y, e, y);
+    }
+    return y;
+}
+template <int STEPS>
+__device__ __forceinline__ double newton_rsqrt(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+#pragma unroll
+    for (int i = 0; i < STEPS; ++i) {
+        const double e = fma(-hx * y, y, 0.5);     // (1 - x y^2) / 2
+        y = fma(y, e, y);
+    }
+    return y;
+}
+
 // Warp-cooperative Householder generation with the xLARFG contract, in FP64
-// whatever the storage type: x (length m <= 64, stride xs, in shared memory)
-// gives beta, tau and v (v[0] = 1) such that (I - tau v v^T) x = (beta, 0..0).
-// tau = 0 when x(1:) == 0.  The norm is scaled by max|x_k|; when |beta| is
-// below safmin the vector is rescaled by 1/safmin (up to 20 times) as in the
-// documented LAPACK algorithm.  Called by all 32 lanes of one warp.
+// whatever the storage type.  x (length m <= 64, contiguous in shared memory)
+// gives beta, tau and v (v[0] = 1) with (I - tau v v^T) x = (beta, 0..0);
+// tau = 0 when x(1:) == 0, and beta = -sign(alpha) ||x|| with sign(+-0) = +1.
+// Overflow and underflow are avoided by scaling x by the power of two sc that
+// brings its largest entry into [1, 4) (exact; it subsumes LAPACK's 1/safmin
+// rescaling loop).  With the scaled vector t = sc x, s2 = ||t||^2 and
+// r = 1/sqrt(s2):
+//   beta = -sign(alpha) s2 r / sc,   tau = 1 + |t0| r,
+//   v_k = vs t_k with vs = sign(alpha) / (|t0| + s2 r).
+// Two entry points so that other warps can work while the FP64 chain runs:
+//   reflector_scale: writes t (in T) to ts[] and returns after that;
+//   reflector_finish: writes v[], tb = {tau, beta, vs}.
+// Both are called by all 32 lanes of one warp, in this order.
+struct ReflScale {
+    double t0, y, a, alpha, inv_hi, inv_lo;   // a = scaled alpha
+    bool zero;   // tail of x is zero: H = I
+};
+
 template <typename T>
-__device__ void warp_reflector(int m, const T* x, int xs, T* v, T* tau_beta)
+__device__ __forceinline__ ReflScale reflector_scale(int m, const T* x, T* ts)
 {
     const int lane = threadIdx.x & 31;
-    const double safmin = 2.2250738585072014e-308 / 2.220446049250313e-16;
-    double x0 = (lane < m) ? (double)x[lane * xs] : 0.0;
-    double x1 = (lane + 32 < m) ? (double)x[(lane + 32) * xs] : 0.0;
-    double alpha = __shfl_sync(FULL, x0, 0);
-    double t0 = (lane >= 1) ? x0 : 0.0;   // tail x(1:)
-    double scale = warp_max(fmax(fabs(t0), fabs(x1)));
-    if (m <= 1 || scale == 0.0) {
+    ReflScale r;
+    const double x0 = (lane < m) ? (double)x[lane] : 0.0;
+    const double x1 = (lane + 32 < m) ? (double)x[lane + 32] : 0.0;
+    r.alpha = __shfl_sync(FULL, x0, 0);
+    const double tl = (lane >= 1) ? x0 : 0.0;   // tail x(1:)
+    r.zero = (m <= 1) || !__any_sync(FULL, tl != 0.0 || x1 != 0.0);
+    auto expo = [](double a) { return (unsigned)(__double_as_longlong(a) >> 52) & 0x7ffu; };
+    unsigned ef = max(max(expo(x0), expo(x1)), 0u);
+    ef = __reduce_max_sync(FULL, ef);
+    double sc_hi, sc_lo = 1.0;
+    r.inv_lo = 1.0;
+    if (ef == 0) {
+        sc_hi = 0x1p1022; sc_lo = 0x1p52; r.inv_hi = 0x1p-1022; r.inv_lo = 0x1p-52;
+    } else {
+        const unsigned es = min(ef, 2045u);
+        sc_hi = __longlong_as_double((long long)(2046u - es) << 52);   // 2^(1023 - es)
+        r.inv_hi = __longlong_as_double((long long)es << 52);          // 2^(es - 1023)
+    }
+    const double s0 = x0 * sc_hi * sc_lo, s1 = x1 * sc_hi * sc_lo;
+    if (lane < m) ts[lane] = (T)s0;
+    if (lane + 32 < m) ts[lane + 32] = (T)s1;
+    r.a = __shfl_sync(FULL, s0, 0);
+    r.t0 = (lane >= 1) ? s0 : 0.0;
+    r.y = s1;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void reflector_finish(int m, const ReflScale& r, T* v, T* tb)
+{
+    const int lane = threadIdx.x & 31;
+    if (r.zero) {
         if (lane < m) v[lane] = (T)(lane == 0 ? 1.0 : 0.0);
         if (lane + 32 < m) v[lane + 32] = (T)0;
-        if (lane == 0) { tau_beta[0] = (T)0; tau_beta[1] = (T)alpha; }
+        if (lane == 0) { tb[0] = (T)0; tb[1] = (T)r.alpha; tb[2] = (T)0; }
         return;
     }
-    double q0 = t0 / scale, q1 = x1 / scale;
-    double xnorm = scale * sqrt(warp_sum(q0 * q0 + q1 * q1));
-    double beta = hypot(alpha, xnorm);
-    if (alpha >= 0.0) beta = -beta;
-    int knt = 0;
-    if (fabs(beta) < safmin) {
-        const double rs = 1.0 / safmin;
-        do {
-            ++knt;
-            t0 *= rs; x1 *= rs; beta *= rs; alpha *= rs;
-        } while (fabs(beta) < safmin && knt < 20);
-        scale = warp_max(fmax(fabs(t0), fabs(x1)));
-        q0 = t0 / scale; q1 = x1 / scale;
-        xnorm = scale * sqrt(warp_sum(q0 * q0 + q1 * q1));
-        beta = hypot(alpha, xnorm);
-        if (alpha >= 0.0) beta = -beta;
+    const double a = r.a;
+    double part = fma(r.t0, r.t0, r.y * r.y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    const double s2 = fma(a, a, part);
+    constexpr int NS = sizeof(T) == 8 ? 2 : 1;   // Newton steps for the storage precision
+    const double rs = newton_rsqrt<NS>(s2);
+    const double nrm = s2 * rs;
+    const double absa = fabs(a);
+    const double tau = fma(absa, rs, 1.0);
+    const double rd = newton_rcp<NS>(absa + nrm);
+    const double sgn = (r.alpha >= 0.0) ? 1.0 : -1.0;
+    const double vs = sgn * rd;
+    if (lane < m) v[lane] = (T)(lane == 0 ? 1.0 : r.t0 * vs);
+    if (lane + 32 < m) v[lane + 32] = (T)(r.y * vs);
+    if (lane == 0) {
+        tb[0] = (T)tau;
+        tb[1] = (T)((-sgn * nrm) * r.inv_hi * r.inv_lo);
+        tb[2] = (T)vs;
     }
-    const double tau = (beta - alpha) / beta;
-    const double scal = 1.0 / (alpha - beta);
-    if (lane < m) v[lane] = (T)(lane == 0 ? 1.0 : t0 * scal);
-    if (lane + 32 < m) v[lane + 32] = (T)(x1 * scal);
-    for (int j = 0; j < knt; ++j) beta *= safmin;
-    if (lane == 0) { tau_beta[0] = (T)tau; tau_beta[1] = (T)beta; }
+}
+
+// Both halves in one call (used where nothing else overlaps).
+template <typename T>
+__device__ __forceinline__ void warp_reflector(int m, const T* x, T* ts, T* v, T* tb)
+{
+    const ReflScale r = reflector_scale<T>(m, x, ts);
+    reflector_finish<T>(m, r, v, tb);
 }
 
 // ----------------------------------------------------------- bounded waits
-// Spin until *addr >= target.  Gives up (sets the error and abort words and
-// returns false) when the watched word has not changed for timeout_ns, or
-// when another CTA aborted.  Called by one thread.
+// Spin until *addr >= target.  The sleep between polls grows with the
+// distance still to go (a far-away target is polled rarely, so hundreds of
+// waiting CTAs do not flood the L2 slice that holds the word).  Gives up (sets
+// the error and abort words and returns false) when the watched word has not
+// changed for timeout_ns, or when another CTA aborted.  Called by one thread.
 __device__ bool wait_at_least(const int* addr, int target, Header* hdr,
                               unsigned long long timeout_ns)
 {
     int last = ld_acquire(addr);
     if (last >= target) return true;
     unsigned long long t_last = global_ns();
-    unsigned backoff = 32;
     for (;;) {
-        __nanosleep(backoff);
-        if (backoff < 256) backoff <<= 1;
-        int v = ld_acquire(addr);
+        const int gap = target - last;
+        __nanosleep(gap > 2 ? 2000u : (gap == 2 ? 400u : 64u));
+        const int v = ld_acquire(addr);
         if (v >= target) return true;
         if (ld_relaxed(&hdr->abort)) return false;
-        unsigned long long now = global_ns();
-        if (v != last) { last = v; t_last = now; backoff = 32; continue; }
+        const unsigned long long now = global_ns();
+        if (v != last) { last = v; t_last = now; continue; }
         if (now - t_last > timeout_ns) {
             atomicOr(&hdr->err, 1 << 4 /* BB_ERR_TIMEOUT */);
             atomicExch(&hdr->abort, 1);

@@ -72,7 +72,7 @@ def test_default_tuning(bb):
     t32 = bb.bb_default_tuning(32768, 128, bb.BB_F32)
     # one 128-byte line per tile row: 16 doubles, 32 floats (Section VI-B)
     assert t64.tw == 16 and t32.tw == 32
-    assert t64.tpb in (64, 128, 256, 512)
+    assert t64.tpb == 0          # 0: sized per stage (two threads per panel row + a reflector warp)
 
 
 def test_host_side_argument_errors(bb):
@@ -87,7 +87,7 @@ def test_host_side_argument_errors(bb):
     assert L.band_to_bidiag(1 << 20, 4, 1, 16, 5, 16, 16, None) == bb.BB_ERR_UNSUPPORTED
     t = bb.Tuning(tw=40)
     assert L.band_to_bidiag_ex(10, 4, 1, 16, 5, 16, 16, ctypes.byref(t), None, 0, None) == bb.BB_ERR_ARG
-    t = bb.Tuning(tpb=100)
+    t = bb.Tuning(tpb=100)     # not a multiple of 32
     assert L.band_to_bidiag_ex(10, 4, 1, 16, 5, 16, 16, ctypes.byref(t), None, 0, None) == bb.BB_ERR_ARG
     # caller workspace too small / misaligned
     ws = bb.band_to_bidiag_workspace_size(100, 8, bb.BB_F64)
@@ -101,5 +101,6 @@ def test_workspace_size_model(bb):
     # working band of height b + 2 TW + 1 (Section V storage format), padded
     n, b = 32768, 128
     ws = bb.band_to_bidiag_workspace_size(n, b, bb.BB_F64)
-    ldw = -(-(b + 2 * 16 + 1) // 4) * 4
-    assert ldw * n * 8 <= ws <= ldw * n * 8 + 4 * n + 4096
+    ldw = -(-(b + 2 * 16) // 4) * 4 + 1          # ldw - 1 a multiple of 4 (16-byte phase)
+    assert ldw >= b + 2 * 16 + 1
+    assert ldw * n * 8 <= ws <= ldw * n * 8 + 128 * n + 4096
