@@ -133,14 +133,17 @@ __device__ __forceinline__ void left_store(const T* LP, T* __restrict__ W, int l
 // D/E: the same for the left reflector (column c) and the left panel's
 //    columns, which are then stored one warp per column.
 // The left panel's tail columns (offset >= tail_start) are the only part the
-// previous sweep's next row-bulge also writes: they are loaded after the wait
-// on it (tail_prog >= tail_target) and updated straight from registers.
+// previous sweep's next row-bulge also writes, and only through its right
+// reflector: they are loaded after that row-bulge has published its right half
+// (tail_prog >= tail_target) and updated straight from registers.  This
+// row-bulge publishes its own right half (half_prog = half_value) after C.
 // Returns false when a wait gave up.
 template <typename T, int MAXM>
 __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int bw, int d, int R,
                                           int s, T* RP, T* LP, T* wbuf, T* tsR, T* tsL, T* vR, T* vL,
                                           T* tb, int* s_flag, const int* tail_prog, int tail_target,
-                                          int tail_start, Header* hdr, unsigned long long timeout_ns)
+                                          int tail_start, Header* hdr, unsigned long long timeout_ns,
+                                          int* half_prog, int half_value)
 {
     constexpr int H = Split<MAXM>::H;
     const int n = D.n, ldw = D.ldw, top = D.top;
@@ -232,6 +235,10 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
         }
     }
     __syncthreads();
+
+    // the right reflector's results outside the left panel are in the working
+    // band: the next sweep's previous row-bulge may now finish its tail
+    if (tid == 0 && half_prog) st_release(half_prog, half_value);
 
     // ---- D: left reflector (warp 0) || column dot products (workers)
     T* tbL = tb + 4;
@@ -355,20 +362,25 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         for (int s = 0; s < ns; ++s) {
             if (tid == 0) {
                 bool w_ok = true;
-                if (R > 0)
-                    w_ok = wait_at_least(&prog[(R - 1) * ps], base + min(s + (split ? 1 : 3), nsp),
-                                         L.hdr, L.timeout_ns);
+                if (R > 0)   // row-bulge s (s+2 when not split) of sweep R-1 complete
+                    w_ok = wait_at_least(&prog[(R - 1) * ps],
+                                         base + 2 * min(s + (split ? 1 : 3), nsp), L.hdr, L.timeout_ns);
                 s_ok = w_ok;
             }
             __syncthreads();
             if (!s_ok) { ok = false; break; }
             const bool step_ok = row_bulge<T, MAXM>(
                 D, W, bw, d, R, s, RP, LP, wbuf, tsR, tsL, vR, vL, tb, &s_tail_ok,
-                (split && R > 0) ? &prog[(R - 1) * ps] : nullptr, base + min(s + 2, nsp),
-                split ? bw - 1 : (1 << 30), L.hdr, L.timeout_ns);
+                (split && R > 0) ? &prog[(R - 1) * ps] : nullptr,
+                // right half of row-bulge s+1 of sweep R-1 (or that sweep complete).
+                // With bw - d == 2 the left half of row-bulge s+1 of sweep R-2 reaches
+                // the tail rows too, so there the whole of row-bulge s+1 is awaited.
+                base + (s + 1 < nsp ? 2 * (s + 1) + (bw - d >= 3 ? 1 : 2) : 2 * nsp),
+                split ? bw - 1 : (1 << 30), L.hdr, L.timeout_ns,
+                stall ? nullptr : &prog[R * ps], base + 2 * s + 1);
             __syncthreads();
             if (!step_ok) { ok = false; break; }
-            if (tid == 0 && !stall) st_release(&prog[R * ps], base + s + 1);   // cumulative release
+            if (tid == 0 && !stall) st_release(&prog[R * ps], base + 2 * s + 2);   // cumulative release
         }
         if (!ok) break;
         if (tid == 0 && !stall && ns == 0) st_release(&prog[R * ps], base);

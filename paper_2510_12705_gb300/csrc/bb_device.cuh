@@ -15,7 +15,7 @@
 namespace bb {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int PROG_STAGE = 1 << 20;   // progress word = stage * PROG_STAGE + steps done
+constexpr int PROG_STAGE = 1 << 20;   // progress word = stage * PROG_STAGE + 2 * row-bulges done (+1: right half of the next)
 
 // --------------------------------------------------------------- memory ops
 template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
