@@ -327,13 +327,16 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
     const int stage = L.stage;
 
     for (;;) {
+        // Tasks go round-robin over the problems (task t: problem t mod count,
+        // sweep t div count), so every problem's sweep chain advances at once;
+        // a task only waits on a smaller task index, so claiming in order
+        // cannot deadlock.
         if (tid == 0) {
             int t = -1;
             if (!ld_relaxed(&L.hdr->abort)) t = atomicAdd(&L.hdr->claim, 1);
-            if (t >= 0 && t < L.sweeps_per_stage) {
-                const int q = find_problem_by_sweep(L, t);
-                s_task[0] = q;
-                s_task[1] = (int)(t - desc_of(L, q).sweep_prefix);
+            if (t >= 0 && t < L.total_tasks) {
+                s_task[0] = t % L.count;
+                s_task[1] = t / L.count;
             } else {
                 s_task[0] = -1;
             }
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         const int R = s_task[1];
         const Desc& D = desc_of(L, q);
         __syncthreads();   // s_task may be rewritten on the next claim
-        if (stage >= D.nstages) continue;
+        if (stage >= D.nstages || R >= D.n - 1) continue;
 
         const int n = D.n;
         const int bw = stage_bw(D.b, L.tw, stage);
@@ -509,7 +512,11 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
     L.single = P->descs[0];
     L.tw = tw;
     L.sweeps_per_stage = sweep_prefix;
-    L.total_tasks = (int64_t)max_stages * sweep_prefix;
+    {
+        int64_t nmax1 = 0;
+        for (const Desc& D : P->descs) nmax1 = std::max<int64_t>(nmax1, D.n - 1);
+        L.total_tasks = (int64_t)count * nmax1;   // tasks of one stage launch
+    }
     L.total_cols = col_prefix;
     L.timeout_ns = P->tune.timeout_ns;
     L.flags = P->tune.flags;
@@ -570,7 +577,7 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
             return BB_ERR_UNSUPPORTED;
         int64_t grid = (int64_t)nsm * per_sm;
         if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
-        grid = std::min<int64_t>(grid, L.sweeps_per_stage);
+        grid = std::min<int64_t>(grid, L.total_tasks);
         if (grid < 1) continue;
         L.stage = stage;
         // each stage restarts the claim counter (a tiny kernel-free reset)

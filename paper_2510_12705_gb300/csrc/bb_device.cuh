@@ -77,7 +77,7 @@ struct Launch {
     int count;            // problems
     int tw;               // inner tilewidth
     int64_t sweeps_per_stage;  // sum over problems of (n - 1)
-    int64_t total_tasks;       // max_stages * sweeps_per_stage
+    int64_t total_tasks;       // tasks of one stage launch: count * max(n - 1)
     int64_t total_cols;        // sum over problems of n
     void* wbase;          // working bands
     int* prog;            // progress words, one per sweep every prog_stride ints

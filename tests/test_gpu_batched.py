@@ -1,0 +1,104 @@
+"""Batched reduction of many band matrices of uneven n and b in one
+persistent launch per stage (bb_batch_plan / bb_batch_execute), including
+capture into a CUDA graph and replay."""
+import numpy as np
+import pytest
+
+import bandgen
+import oracle
+from gpu_util import TOL_F32, TOL_F64
+
+pytestmark = pytest.mark.gpu
+
+
+def _make(problems, dtype):
+    import torch
+    out = []
+    for (n, b, seed) in problems:
+        ab = bandgen.random_band(n, b, seed=seed)
+        band = torch.from_numpy(ab).to("cuda", dtype)
+        d = torch.full((n,), float("nan"), device="cuda", dtype=dtype)
+        e = torch.full((max(n - 1, 1),), float("nan"), device="cuda", dtype=dtype)
+        out.append((band, b, d, e, ab))
+    return out
+
+
+def _single(band, b, dtype):
+    import torch
+    import paper_2510_12705_gb300 as bb
+    n = band.shape[0]
+    d = torch.empty(n, device="cuda", dtype=dtype)
+    e = torch.empty(max(n - 1, 1), device="cuda", dtype=dtype)
+    bb.band_to_bidiag(band, b, d, e)
+    return d.cpu().numpy(), e[: n - 1].cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype_name", ["f64", "f32"])
+def test_batch_matches_single_and_oracle(dtype_name):
+    import torch
+    import paper_2510_12705_gb300 as bb
+    dtype = torch.float64 if dtype_name == "f64" else torch.float32
+    tol = TOL_F64 if dtype_name == "f64" else TOL_F32
+    probs = bandgen.batch_problems(24, seed=3, n_lo=40, n_hi=700, bands=(1, 8, 16, 32, 64)) + \
+        [(1, 0, 5), (2, 1, 6), (3, 2, 7), (50, 80, 8)]          # tiny and b >= n
+    items = _make(probs, dtype)
+    plan = bb.BatchPlan([(band, b, d, e) for band, b, d, e, _ in items])
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.execute(ws)
+    torch.cuda.synchronize()
+    assert bb.bb_device_status(reset=True) == 0
+    for (band, b, d, e, ab) in items:
+        n = band.shape[0]
+        dg, eg = d.cpu().numpy(), e[: n - 1].cpu().numpy()
+        ds, es = _single(band, b, dtype)
+        # same kernels and reflector sequence: bitwise equal to the single call
+        assert np.array_equal(dg, ds) and np.array_equal(eg, es), (n, b)
+        d0, e0, _ = oracle.band_to_bidiag(ab, b, 16)
+        s0 = oracle.bidiag_sigma(d0, e0)
+        s = oracle.bidiag_sigma(dg.astype(np.float64), eg.astype(np.float64))
+        assert np.max(np.abs(s - s0)) <= tol * max(s0[0], 1e-300), (n, b)
+
+
+def test_batch_graph_capture_and_replay():
+    import torch
+    import paper_2510_12705_gb300 as bb
+    dtype = torch.float32
+    probs = bandgen.batch_problems(16, seed=9, n_lo=100, n_hi=900, bands=(8, 16, 32, 64))
+    items = _make(probs, dtype)
+    plan = bb.BatchPlan([(band, b, d, e) for band, b, d, e, _ in items])
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):          # warm-up outside the capture (module loading)
+        plan.execute(ws, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.execute(ws)
+    for rep in range(2):
+        # new inputs in the captured buffers, then replay
+        refs = []
+        for j, (band, b, d, e, _) in enumerate(items):
+            n = band.shape[0]
+            ab = bandgen.random_band(n, b, seed=1000 * rep + j)
+            band.copy_(torch.from_numpy(ab).to(dtype))
+            refs.append(ab)
+        g.replay()
+        torch.cuda.synchronize()
+        assert bb.bb_device_status(reset=True) == 0
+        for (band, b, d, e, _), ab in zip(items, refs):
+            n = band.shape[0]
+            ds, es = _single(band, b, dtype)
+            assert np.array_equal(d.cpu().numpy(), ds)
+            assert np.array_equal(e[: n - 1].cpu().numpy(), es)
+
+
+def test_batch_plan_rejects_bad_problem():
+    import torch
+    import paper_2510_12705_gb300 as bb
+    band = torch.zeros((10, 3), device="cuda", dtype=torch.float64)
+    d = torch.empty(10, device="cuda", dtype=torch.float64)
+    e = torch.empty(9, device="cuda", dtype=torch.float64)
+    with pytest.raises(bb.BBError):
+        bb.BatchPlan([(band, 5, d, e)])        # ldab = 3 < b + 1
