@@ -14,10 +14,10 @@ As a numpy array of shape (n, ldab) (one row per matrix column), that is
 ``ab2d[j, b + i - j]``.  Entries of ``ab`` that fall outside the matrix
 (i < 0) are zero.
 
-The workloads follow the paper's synthetic inputs: random bands with iid
-N(0, 1) entries (Section V), graded rows that stress small singular values,
-a structured closed-form instance, and matrices with prescribed singular
-values (Section VI-A, the accuracy experiment).
+The workloads: random bands with iid N(0, 1) entries (the paper times
+synthetic bands without stating their distribution), graded rows that stress
+small singular values, a structured closed-form instance, and matrices with
+prescribed singular values (Section V-A, the accuracy experiment).
 """
 from __future__ import annotations
 

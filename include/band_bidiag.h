@@ -59,7 +59,7 @@ extern "C" {
                                         run out and the call records BB_ERR_TIMEOUT */
 
 /*
- * Kernel hyperparameters (Section IV-C): zero selects the built-in default.
+ * Kernel hyperparameters (Section III-C): zero selects the built-in default.
  *   tw               inner tilewidth TW: bandwidth removed per stage (1..32)
  *   tpb              threads per bulge (CTA size: 64, 128, 256 or 512)
  *   sweeps_in_flight persistent CTAs, i.e. sweeps processed concurrently
@@ -92,9 +92,10 @@ typedef struct {
 } bb_problem;
 
 /*
- * band_to_bidiag -- reduce one band matrix (Algorithm 1 over all stages,
- * one persistent launch).  The workspace (working band with fill rows of
- * height b + 2 TW + 1, Section V storage format, plus progress counters) is
+ * band_to_bidiag -- reduce one band matrix (Algorithm 1 over all stages:
+ * a pack kernel, one persistent launch per stage, an extract kernel).  The
+ * workspace (working band with fill rows of
+ * height b + 2 TW + 1, Section IV storage format, plus progress counters) is
  * taken from CUDA's stream-ordered allocator on `stream` and released on it.
  */
 int band_to_bidiag(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab,
@@ -112,6 +113,15 @@ int band_to_bidiag_ex(int64_t n, int64_t b, int dtype, const void *band, int64_t
 
 /* bytes of workspace band_to_bidiag_ex needs for this problem and tuning */
 size_t band_to_bidiag_workspace_size(int64_t n, int64_t b, int dtype, const bb_tuning *tuning);
+
+/*
+ * dynamic shared memory per CTA of the bulge kernel for this problem and
+ * tuning (both panels of a row-bulge); host only, 0 on invalid arguments.  A
+ * tuning is usable on a device when this is at most the device's opt-in
+ * shared memory per block (227 KB on sm_103a); otherwise the calls return
+ * BB_ERR_UNSUPPORTED.
+ */
+size_t bb_shared_bytes(int64_t n, int64_t b, int dtype, const bb_tuning *tuning);
 
 /*
  * band_to_bidiag_host -- end-to-end call on HOST buffers: copies the band
@@ -176,6 +186,49 @@ int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning *out);
  */
 double bb_measure_l2_bandwidth(size_t bytes, int reps, void *stream);
 double bb_measure_fma_peak(int dtype, void *stream);
+
+/*
+ * Tuning (Section III-C hyperparameters; Section IV brute-force search;
+ * automatic tuning is the paper's future work, Section VII).
+ *
+ * bb_autotune -- exhaustive search: reduces the caller's problem once untimed,
+ * then `reps` times timed (CUDA events, median) for each of the `ncand`
+ * candidate tunings (host array), writes the median times (ms) to times_ms
+ * (host, ncand) and the index of the fastest to *best.  A candidate the
+ * problem cannot use (BB_ERR_UNSUPPORTED, e.g. panels larger than shared
+ * memory) gets time +inf; BB_ERR_UNSUPPORTED is returned only when no
+ * candidate runs.  band/d_out/e_out as in band_to_bidiag (d_out, e_out are
+ * overwritten).  Synchronous; allocates one workspace from the stream-ordered
+ * allocator.
+ */
+int bb_autotune(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab, void *d_out,
+                void *e_out, const bb_tuning *candidates, int ncand, int reps, float *times_ms,
+                int *best, void *stream);
+
+/*
+ * Learned tuner: a multilayer perceptron in_dim -> hidden -> hidden -> 1 with
+ * ReLU activations, FP32, trained with mean squared error and Adam.  All
+ * pointers are device pointers; all calls are asynchronous on `stream`.
+ * Parameters (bb_mlp_param_count floats, row-major weights):
+ *   W1[hidden][in_dim] | b1[hidden] | W2[hidden][hidden] | b2[hidden] | W3[hidden] | b3
+ * Requires 1 <= in_dim <= 32 and in_dim <= hidden <= 128, hidden % 32 == 0.
+ *   bb_mlp_forward:  X[N][in_dim] -> Y[N]; saves the activations H1, H2 [N][hidden].
+ *   bb_mlp_backward: gradient of (1/N) sum (Y - T)^2 with respect to every
+ *                    parameter into grads; scratch holds
+ *                    bb_mlp_backward_scratch(hidden, N) floats.
+ *   bb_mlp_adam:     one Adam step (bias-corrected, step >= 1) on `count`
+ *                    parameters with moment buffers m, v.
+ * Return BB_OK, BB_ERR_ARG or BB_ERR_LAUNCH.
+ */
+size_t bb_mlp_param_count(int in_dim, int hidden);
+size_t bb_mlp_backward_scratch(int hidden, int N);
+int bb_mlp_forward(int in_dim, int hidden, const float *params, const float *X, int N, float *Y,
+                   float *H1, float *H2, void *stream);
+int bb_mlp_backward(int in_dim, int hidden, const float *params, const float *X, const float *H1,
+                    const float *H2, const float *Y, const float *T, int N, float *grads,
+                    float *scratch, void *stream);
+int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v, int step,
+                float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
  * band_to_bidiag_noalloc -- the paper has no counterpart; this is a library

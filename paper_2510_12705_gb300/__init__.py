@@ -75,6 +75,7 @@ def lib():
             "band_to_bidiag": (ci, [i64, i64, ci, vp, i64, vp, vp, vp]),
             "band_to_bidiag_ex": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, vp, sz, vp]),
             "band_to_bidiag_workspace_size": (sz, [i64, i64, ci, tp]),
+            "bb_shared_bytes": (sz, [i64, i64, ci, tp]),
             "band_to_bidiag_host": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, vp]),
             "bb_batch_plan_create": (vp, [ci, ctypes.POINTER(Problem), ci, tp]),
             "bb_batch_plan_workspace_size": (sz, [vp]),
@@ -88,6 +89,14 @@ def lib():
             "bb_default_tuning": (ci, [i64, i64, ci, tp]),
             "bb_measure_l2_bandwidth": (ctypes.c_double, [sz, ci, vp]),
             "bb_measure_fma_peak": (ctypes.c_double, [ci, vp]),
+            "bb_autotune": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, ci, ci,
+                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci), vp]),
+            "bb_mlp_param_count": (sz, [ci, ci]),
+            "bb_mlp_backward_scratch": (sz, [ci, ci]),
+            "bb_mlp_forward": (ci, [ci, ci, vp, vp, ci, vp, vp, vp, vp]),
+            "bb_mlp_backward": (ci, [ci, ci, vp, vp, vp, vp, vp, vp, ci, vp, vp, vp]),
+            "bb_mlp_adam": (ci, [ci, vp, vp, vp, vp, ci, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -170,6 +179,11 @@ def band_to_bidiag_workspace_size(n: int, b: int, dtype: int, tuning=None) -> in
     return int(lib().band_to_bidiag_workspace_size(n, b, dtype, _tuning_ptr(tuning)))
 
 
+def bb_shared_bytes(n: int, b: int, dtype: int, tuning=None) -> int:
+    """Dynamic shared memory per CTA of the bulge kernel (0 = invalid)."""
+    return int(lib().bb_shared_bytes(n, b, dtype, _tuning_ptr(tuning)))
+
+
 def band_to_bidiag_host(band, b: int, tuning=None, stream=None, out=None):
     """End-to-end call on host numpy arrays (pinned if possible): returns (d, e)."""
     import numpy as np
@@ -237,7 +251,8 @@ def bb_measure_fma_peak(dtype: int, stream=None) -> float:
 
 
 class BatchPlan:
-    """bb_batch_plan: many band problems reduced in one persistent launch.
+    """bb_batch_plan: many band problems reduced together, one persistent launch
+    per stage for all of them.
 
     ``problems``: list of (band, b, d_out, e_out) CUDA tensors of one dtype.
     ``execute(workspace, stream)`` only enqueues stream work, so it can be
@@ -290,3 +305,48 @@ def band_to_bidiag_noalloc(band, b: int, d_out, e_out, stream=None) -> None:
     rc = f(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab, d_out.data_ptr(),
            e_out.data_ptr() if n > 1 else None, _stream_handle(stream))
     _check(rc, "band_to_bidiag_noalloc")
+
+
+def bb_autotune(band, b: int, d_out, e_out, candidates, reps: int = 1, stream=None):
+    """Exhaustive search: time every Tuning in ``candidates`` on this problem
+    (median of ``reps`` runs after one untimed run); returns (times_ms, best)."""
+    n, ldab = _check_band(band, d_out, e_out)
+    arr = (Tuning * len(candidates))(*candidates)
+    times = (ctypes.c_float * len(candidates))()
+    best = ctypes.c_int(-1)
+    rc = lib().bb_autotune(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab, d_out.data_ptr(),
+                           e_out.data_ptr() if n > 1 else None, arr, len(candidates), reps, times,
+                           ctypes.byref(best), _stream_handle(stream))
+    _check(rc, "bb_autotune")
+    return [float(t) for t in times], int(best.value)
+
+
+def bb_mlp_param_count(in_dim: int, hidden: int) -> int:
+    return int(lib().bb_mlp_param_count(in_dim, hidden))
+
+
+def bb_mlp_backward_scratch(hidden: int, N: int) -> int:
+    return int(lib().bb_mlp_backward_scratch(hidden, N))
+
+
+def bb_mlp_forward(in_dim: int, hidden: int, params, X, Y, H1, H2, stream=None) -> None:
+    """Y[N], H1[N][hidden], H2[N][hidden] from X[N][in_dim] (FP32 CUDA tensors)."""
+    rc = lib().bb_mlp_forward(in_dim, hidden, params.data_ptr(), X.data_ptr(), X.shape[0],
+                              Y.data_ptr(), H1.data_ptr(), H2.data_ptr(), _stream_handle(stream))
+    _check(rc, "bb_mlp_forward")
+
+
+def bb_mlp_backward(in_dim: int, hidden: int, params, X, H1, H2, Y, T, grads, scratch,
+                    stream=None) -> None:
+    """Gradient of mean((Y - T)^2) with respect to the flat parameters."""
+    rc = lib().bb_mlp_backward(in_dim, hidden, params.data_ptr(), X.data_ptr(), H1.data_ptr(),
+                               H2.data_ptr(), Y.data_ptr(), T.data_ptr(), X.shape[0],
+                               grads.data_ptr(), scratch.data_ptr(), _stream_handle(stream))
+    _check(rc, "bb_mlp_backward")
+
+
+def bb_mlp_adam(params, grads, m, v, step: int, lr: float, beta1: float = 0.9,
+                beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    rc = lib().bb_mlp_adam(params.numel(), params.data_ptr(), grads.data_ptr(), m.data_ptr(),
+                           v.data_ptr(), step, lr, beta1, beta2, eps, _stream_handle(stream))
+    _check(rc, "bb_mlp_adam")

@@ -1,15 +1,18 @@
 // Band -> bidiagonal reduction by Householder bulge chasing on sm_103a
 // (arXiv 2510.12705, Section III: Algorithm 1 schedule, Algorithm 2 row-bulge).
 //
-// One persistent launch runs every stage of every problem.  CTAs claim tasks
-// (stage, problem, sweep) in order from a global counter; a task runs the
-// row-bulges of one sweep.  Consecutive sweeps of a stage are separated by
-// the dependency distance of Section III-A: sweep R may start row-bulge s
-// once sweep R-1 has finished row-bulge s + L - 1, with L = 2 when the
-// post-stage bandwidth is at least 2 and L = 3 otherwise.  Stage i+1 of a
-// problem starts once all sweeps of stage i have finished.  Because tasks are
-// claimed in order and only wait on earlier tasks, the schedule cannot
-// deadlock however many CTAs are resident.  Every wait is bounded.
+// One persistent launch per bandwidth-reduction stage runs that stage for
+// every problem of the call.  CTAs claim tasks (problem, sweep) from a global
+// counter, round-robin over the problems; a task runs the row-bulges of one
+// sweep.  Consecutive sweeps of a stage are separated by the dependency
+// distance of Section III-A: sweep R may start row-bulge s once sweep R-1 has
+// finished row-bulge s + L - 1, with L = 2 when the post-stage bandwidth is at
+// least 2 and L = 3 otherwise (on split stages a half-step progress mark lets
+// the left half of the next row-bulge start earlier).  Stage i+1 starts when
+// the launch of stage i has ended (stream order, the paper's stage barrier).
+// Because tasks are claimed in order and only wait on earlier tasks, the
+// schedule cannot deadlock however many CTAs are resident.  Every wait is
+// bounded.
 //
 // A row-bulge stages its right panel (rows r0..c+m-1 x columns c..c+m-1) and
 // left panel (rows c..c+m-1 x columns c..jmax) in shared memory, builds each
@@ -670,6 +673,14 @@ size_t band_to_bidiag_workspace_size(int64_t n, int64_t b, int dtype, const bb_t
     LaunchPlan P;
     if (plan_launch(1, &p, dtype, tuning, &P) != BB_OK) return 0;
     return P.bytes;
+}
+
+size_t bb_shared_bytes(int64_t n, int64_t b, int dtype, const bb_tuning* tuning)
+{
+    bb_problem p = {n, b, (const void*)16, b + 1, (void*)16, (void*)16};
+    LaunchPlan P;
+    if (plan_launch(1, &p, dtype, tuning, &P) != BB_OK) return 0;
+    return P.smem;
 }
 
 int band_to_bidiag_ex(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab,

@@ -2,7 +2,7 @@
 //
 // Working storage: every problem owns a band-with-fill buffer in column-major
 // band layout, element (i, j) at W[(i - j + top) + j * ldw], top = b + TW,
-// ldw >= b + 2 TW + 1 (the band of height BW + 2 TW of Section V).  A column's
+// ldw >= b + 2 TW + 1 (the band of height BW + 2 TW of Section IV).  A column's
 // band segment is contiguous, so the right panel of a row-bulge (rows x
 // TW+1 columns) and the left panel (TW+1 rows x columns) are both runs of
 // contiguous column segments.  Shared-working-buffer traffic goes through L2

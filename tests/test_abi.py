@@ -70,7 +70,7 @@ def test_work_model_large_is_fast_and_consistent(bb):
 def test_default_tuning(bb):
     t64 = bb.bb_default_tuning(32768, 128, bb.BB_F64)
     t32 = bb.bb_default_tuning(32768, 128, bb.BB_F32)
-    # one 128-byte line per tile row: 16 doubles, 32 floats (Section VI-B)
+    # one 128-byte line per tile row: 16 doubles, 32 floats (Section V-B)
     assert t64.tw == 16 and t32.tw == 32
     assert t64.tpb == 0          # 0: sized per stage (two threads per panel row + a reflector warp)
 
@@ -97,8 +97,55 @@ def test_host_side_argument_errors(bb):
     assert bb.status_string(bb.BB_ERR_TIMEOUT) == "device wait timed out"
 
 
+def test_tuning_entry_points_host_checks(bb):
+    L = bb.lib()
+    D, H = 8, 32
+    assert bb.bb_mlp_param_count(D, H) == H * D + H + H * H + H + H + 1
+    assert bb.bb_mlp_param_count(8, 48) == 0          # hidden must be a multiple of 32
+    assert bb.bb_mlp_param_count(33, 64) == 0         # in_dim <= 32
+    assert bb.bb_mlp_param_count(0, 32) == 0
+    assert bb.bb_mlp_backward_scratch(H, 10) == 10 * (1 + 2 * H)
+    # validation happens before any CUDA call
+    assert L.bb_mlp_forward(D, H, None, 16, 4, 16, 16, 16, None) == bb.BB_ERR_ARG
+    assert L.bb_mlp_forward(D, 40, 16, 16, 4, 16, 16, 16, None) == bb.BB_ERR_ARG
+    assert L.bb_mlp_backward(D, H, 16, 16, 16, 16, 16, 16, 0, 16, 16, None) == bb.BB_ERR_ARG
+    assert L.bb_mlp_adam(0, 16, 16, 16, 16, 1, 1e-3, 0.9, 0.999, 1e-8, None) == bb.BB_ERR_ARG
+    assert L.bb_mlp_adam(10, 16, 16, 16, 16, 0, 1e-3, 0.9, 0.999, 1e-8, None) == bb.BB_ERR_ARG
+    times = (ctypes.c_float * 1)()
+    best = ctypes.c_int()
+    assert L.bb_autotune(100, 8, 1, 16, 9, 16, 16, None, 1, 1, times, ctypes.byref(best),
+                         None) == bb.BB_ERR_ARG
+    cand = (bb.Tuning * 1)(bb.Tuning(tw=16))
+    assert L.bb_autotune(100, 8, 1, 16, 9, 16, 16, cand, 0, 1, times, ctypes.byref(best),
+                         None) == bb.BB_ERR_ARG
+    assert L.bb_autotune(100, 8, 1, 16, 9, 16, 16, cand, 1, 0, times, ctypes.byref(best),
+                         None) == bb.BB_ERR_ARG
+    bad = (bb.Tuning * 1)(bb.Tuning(tw=64))
+    assert L.bb_autotune(100, 8, 1, 16, 9, 16, 16, bad, 1, 1, times, ctypes.byref(best),
+                         None) == bb.BB_ERR_ARG
+
+
+def test_shared_bytes_model(bb):
+    # both panels of a row-bulge: (MAXM + 1) x (b + TW + 2) elements each
+    assert bb.bb_shared_bytes(4096, 128, bb.BB_F64, bb.Tuning(tw=16)) == 8 * 18 * 2 * (128 + 16 + 2)
+    assert bb.bb_shared_bytes(4096, 512, bb.BB_F32, bb.Tuning(tw=32)) == 4 * 34 * 2 * (512 + 32 + 2)
+    assert bb.bb_shared_bytes(4096, 512, bb.BB_F64, bb.Tuning(tw=32)) > 227 * 1024
+    assert bb.bb_shared_bytes(0, 4, bb.BB_F64) == 0
+
+
+def test_tuner_features_and_grid():
+    from paper_2510_12705_gb300 import tuner
+    c = tuner.candidates()
+    assert len(c) == len(set(c)) == len(tuner.TWS) * len(tuner.TPBS) * len(tuner.SIFS)
+    f = tuner.features(65536, 256, "f32", c[0])
+    assert len(f) == tuner.IN_DIM and all(abs(x) < 4 for x in f)
+    g = tuner.default_grid()
+    assert all(b <= n // 4 and n * b <= (1 << 22) for n, b, _ in g)
+    assert (65536, 256, "f32") not in g
+
+
 def test_workspace_size_model(bb):
-    # working band of height b + 2 TW + 1 (Section V storage format), padded
+    # working band of height b + 2 TW + 1 (Section IV storage format), padded
     n, b = 32768, 128
     ws = bb.band_to_bidiag_workspace_size(n, b, bb.BB_F64)
     ldw = -(-(b + 2 * 16) // 4) * 4 + 1          # ldw - 1 a multiple of 4 (16-byte phase)

@@ -100,7 +100,7 @@ def test_repeatable_bitwise():
 @pytest.mark.parametrize("profile", ["arithmetic", "logarithmic", "quartercircle"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_prescribed_sigma(profile, dtype):
-    # Section VI-A methodology: known singular values in [0, 1]
+    # Section V-A methodology: known singular values in [0, 1]
     ab, sig = bandgen.prescribed_sigma_band(512, 32, profile, seed=11)
     d, e, st = run_gpu(ab, 32, dtype)
     assert st == 0

@@ -50,6 +50,29 @@ def test_bidiag_sigma_closed_form_all_ones():
         assert np.max(np.abs(s - ref)) < 1e-14 * 2, n
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    return np.loadtxt(os.path.join(GOLDEN, name), comments="#")
+
+
+def test_golden_bidiag_ones():
+    # stored closed form (tests/golden/make_golden.py)
+    s = oracle.bidiag_sigma(np.ones(10), np.ones(9), method="bisect")
+    assert np.max(np.abs(s - _golden("bidiag_ones_sigma_n10.txt"))) < 4e-15
+
+
+def test_golden_toeplitz_reduction():
+    # the whole reduction of Toeplitz R (b = 2 and b = 64 storage, several TW)
+    # against the stored closed form
+    ref = _golden("toeplitz_sigma_n64.txt")
+    for b, tw in ((2, 1), (2, 16), (64, 16), (64, 5)):
+        d, e, _ = oracle.band_to_bidiag(bandgen.toeplitz_qr_band(64, b), b, tw)
+        s = oracle.bidiag_sigma(d, e, method="bisect")
+        assert np.max(np.abs(s - ref)) <= 1e-14 * ref[0], (b, tw)
+
+
 def test_bidiag_sigma_against_numpy_and_lapack():
     rng = np.random.default_rng(11)
     for n in (3, 50, 400):
@@ -125,7 +148,7 @@ def test_toeplitz_closed_form(n, b):
 
 @pytest.mark.parametrize("profile", ["arithmetic", "logarithmic", "quartercircle"])
 def test_prescribed_sigma(profile):
-    # Section VI-A: known singular values survive the band reduction
+    # Section V-A: known singular values survive the band reduction
     ab, sig = bandgen.prescribed_sigma_band(128, 12, profile, seed=7)
     d, e, _ = oracle.band_to_bidiag(ab, 12, 4)
     s = oracle.bidiag_sigma(d, e)
