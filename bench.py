@@ -34,6 +34,7 @@ METRIC = "band->bidiag effective GFLOP/s at n=32768, b=128 (FP64; FP32 form alon
 L2_FLUSH_BYTES = 256 << 20
 ORACLE_SAMPLE_STEPS = 600_000        # row-bulges of the first stage (~10-30 s of CPU work)
 REF_STEP_SAMPLE = 150_000            # per --impl reference step
+TUNER_MODEL = os.path.join(ROOT, "paper_2510_12705_gb300", "tuner_model.json")
 
 
 def _peaks_file():
@@ -132,6 +133,21 @@ def run_reference(args, rank, world):
     return 0
 
 
+def pick_tuning(bb, torch, dev, n, b, dtype_code):
+    """Hyperparameters for the timed reduction: the learned tuner's pick (one
+    forward pass of the trained MLP on this GPU, outside the timed region), or
+    the library default when no trained model is present."""
+    t = bb.bb_default_tuning(n, b, dtype_code)
+    if not os.path.exists(TUNER_MODEL):
+        return t, "library default"
+    from paper_2510_12705_gb300 import tuner
+    tw, tpb, sif = tuner.MlpTuner.load(TUNER_MODEL).predict(
+        n, b, "f64" if dtype_code == bb.BB_F64 else "f32")
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return bb.Tuning(tw=tw, tpb=tpb, sweeps_in_flight=nsm if sif else 0,
+                     timeout_s=t.timeout_s), "learned tuner"
+
+
 def run_ours(args, rank, world):
     import torch
     import bandgen
@@ -157,8 +173,8 @@ def run_ours(args, rank, world):
     e32 = torch.empty(n - 1, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    t64 = bb.bb_default_tuning(n, b, bb.BB_F64)
-    t32 = bb.bb_default_tuning(n, b, bb.BB_F32)
+    t64, src64 = pick_tuning(bb, torch, dev, n, b, bb.BB_F64)
+    t32, src32 = pick_tuning(bb, torch, dev, n, b, bb.BB_F32)
     work64 = bb.bb_schedule_counts(n, b, t64.tw)
     work32 = bb.bb_schedule_counts(n, b, t32.tw)
 
@@ -277,7 +293,7 @@ def run_ours(args, rank, world):
         "ms_per_step": ms32, "kernel_ms": ms32_kern,
         "gflops": work32.flops / (ms32 * 1e-3) / 1e9,
         "speedup_vs_fp64": ms_step / ms32,
-        "tw": t32.tw,
+        "tw": t32.tw, "tpb": t32.tpb, "sweeps_in_flight": t32.sweeps_in_flight, "tuning": src32,
         "roofline": {"bound": "l2", "achieved": achieved_l2_32, "peak": l2_gbs, "unit": "GB/s",
                      "frac": achieved_l2_32 / l2_gbs if l2_gbs > 0 else None,
                      "alu_frac": (work32.flops / (ms32_kern * 1e-3) / 1e9) / fp32_peak
@@ -300,6 +316,7 @@ def run_ours(args, rank, world):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"band->bidiag n={n} b={b} FP64 TW={t64.tw}, iid N(0,1) band, seed {SEED}",
                        "n": n, "b": b, "tw": t64.tw, "tpb": t64.tpb,
+                       "sweeps_in_flight": t64.sweeps_in_flight, "tuning": src64,
                        "stages": work64.stages, "row_bulges": work64.steps,
                        "flops_per_step": work64.flops, "algorithmic_bytes_per_step": bytes64,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas"},

@@ -6,9 +6,10 @@
 // counter, round-robin over the problems; a task runs the row-bulges of one
 // sweep.  Consecutive sweeps of a stage are separated by the dependency
 // distance of Section III-A: sweep R may start row-bulge s once sweep R-1 has
-// finished row-bulge s + L - 1, with L = 2 when the post-stage bandwidth is at
-// least 2 and L = 3 otherwise (on split stages a half-step progress mark lets
-// the left half of the next row-bulge start earlier).  Stage i+1 starts when
+// finished row-bulge s + L - 2, and the part of its left panel that row-bulge
+// s + L - 1 of sweep R-1 also touches waits for that row-bulge's right half
+// (a half-step progress mark), with L = 2 when the post-stage bandwidth is at
+// least 2 and L = 3 otherwise.  Stage i+1 starts when
 // the launch of stage i has ended (stream order, the paper's stage barrier).
 // Because tasks are claimed in order and only wait on earlier tasks, the
 // schedule cannot deadlock however many CTAs are resident.  Every wait is
@@ -16,7 +17,7 @@
 //
 // A row-bulge stages its right panel (rows r0..c+m-1 x columns c..c+m-1) and
 // left panel (rows c..c+m-1 x columns c..jmax) in shared memory, builds each
-// reflector with one warp (FP64 generation), applies it with one thread per
+// reflector with one warp (FP64 generation), applies it with two threads per
 // row / column, and writes both panels back through L2.
 #include <algorithm>
 #include <cmath>
@@ -110,16 +111,17 @@ __device__ __forceinline__ int fast_div(int e, int div, float inv)
     return q;
 }
 
-// left-panel columns jj in [lo, hi) back to the working band (exact rows)
+// left-panel columns jj in [lo, hi) back to the working band (exact rows):
+// element e of the block goes to row e mod m of column lo + e / m, so
+// consecutive threads write consecutive rows of a column
 template <typename T, int MAXM>
 __device__ __forceinline__ void left_store(const T* LP, T* __restrict__ W, int ldw, int top, int c,
                                            int m, int lo, int hi)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int jj = lo + warp; jj < hi; jj += nw) {
-        T* col = W + (int64_t)(c + jj) * ldw + (top - jj);
-        if (lane < m) stcg(col + lane, LP[jj * MAXM + lane]);
-        if (MAXM > 32 && lane + 32 < m) stcg(col + lane + 32, LP[jj * MAXM + lane + 32]);
+    const float invM = 1.0f / (float)m;
+    for (int e = threadIdx.x; e < (hi - lo) * m; e += blockDim.x) {
+        const int q = fast_div(e, m, invM), k = e - q * m, jj = lo + q;
+        stcg(W + (int64_t)(c + jj) * ldw + (top - jj + k), LP[jj * MAXM + k]);
     }
 }
 
@@ -146,7 +148,7 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
                                           int s, T* RP, T* LP, T* wbuf, T* tsR, T* tsL, T* vR, T* vL,
                                           T* tb, int* s_flag, const int* tail_prog, int tail_target,
                                           int tail_start, Header* hdr, unsigned long long timeout_ns,
-                                          int* half_prog, int half_value)
+                                          int* half_prog, int half_value, bool carried, bool carry_out)
 {
     constexpr int H = Split<MAXM>::H;
     const int n = D.n, ldw = D.ldw, top = D.top;
@@ -162,45 +164,38 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
     const int p = tid & 1, k0 = p * H;
     const int pre_hi = min(tail_start, ncols + 1);   // left-panel columns loaded up front
 
-    // ---- A: loads
+    // ---- A: loads (with `carried`, panel rows 0..d are already in RP: the
+    //      previous row-bulge's m = d + 1 rows, also where this one's m is
+    //      smaller at the end of the matrix).  Every element is one cp.async,
+    //      so all of a thread's copies are in flight at once.
     {
-        constexpr int U = sizeof(T) == 8 ? 8 : 12;
-        const int totR = nr * m, totL = (pre_hi - m) * m, tot = totR + totL;
-        const float invR = 1.0f / (float)nr, invM = 1.0f / (float)m;
-        for (int base = tid; base < tot; base += U * nt) {
-            T val[U];
-            int dst[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = base + u * nt;
-                dst[u] = -1;
-                if (e < totR) {
-                    const int k = fast_div(e, nr, invR), ri = e - k * nr;
-                    val[u] = ldcg(W + (int64_t)(c + k) * ldw + (r0 + ri - c - k + top));
-                    dst[u] = ri * MAXM + k;
-                } else if (e < tot) {
-                    const int f = e - totR;
-                    const int q = fast_div(f, m, invM), k = f - q * m, jj = m + q;
-                    val[u] = ldcg(W + (int64_t)(c + jj) * ldw + (top - jj + k));
-                    dst[u] = -2 - (jj * MAXM + k);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (dst[u] >= 0) RP[dst[u]] = val[u];
-                else if (dst[u] <= -2) LP[-2 - dst[u]] = val[u];
+        const int ri_lo = carried ? d + 1 : 0, nrl = nr - ri_lo;
+        const int totR = nrl * m, totL = (pre_hi - m) * m, tot = totR + totL;
+        const float invR = 1.0f / (float)max(nrl, 1), invM = 1.0f / (float)m;
+        for (int e = tid; e < tot; e += nt) {
+            if (e < totR) {
+                const int k = fast_div(e, nrl, invR), ri = ri_lo + e - k * nrl;
+                cp_async_elem(RP + ri * MAXM + k, W + (int64_t)(c + k) * ldw + (r0 + ri - c - k + top));
+            } else {
+                const int f = e - totR;
+                const int q = fast_div(f, m, invM), k = f - q * m, jj = m + q;
+                cp_async_elem(LP + jj * MAXM + k, W + (int64_t)(c + jj) * ldw + (top - jj + k));
             }
         }
+        cp_async_wait_all();
     }
     __syncthreads();
 
-    // ---- B: right reflector (warp 0) || row dot products (workers)
+    // ---- B: right reflector (warp 0; already built when `carried`) || row dot
+    //      products (workers)
     if (warp == 0) {
-        const ReflScale sc = reflector_scale<T>(m, RP, tsR);
-        bar_arrive(1, nt);
-        reflector_finish<T>(m, sc, vR, tb);
+        if (!carried) {
+            const ReflScale sc = reflector_scale<T>(m, RP, tsR);
+            bar_arrive(1, nt);
+            reflector_finish<T>(m, sc, vR, tb);
+        }
     } else {
-        bar_sync_n(1, nt);
+        if (!carried) bar_sync_n(1, nt);
         for (int ri = 1 + (wt >> 1); ri - (wt >> 1) < nr; ri += nwt >> 1) {
             T w = (T)0;
             if (ri < nr) {
@@ -279,7 +274,16 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
         }
     }
     __syncthreads();
-    left_store<T, MAXM>(LP, W, ldw, top, c, m, 0, pre_hi);
+    // With `carry_out`, left-panel columns bw .. bw+m'-1 are the next row-bulge's
+    // right panel rows 0..m-1 (its bulge row is row c): they stay in RP (free
+    // since C) instead of a round trip through L2; the next row-bulge writes
+    // them back in its phase C, before any other sweep may read them.
+    const int keep_lo = carry_out ? min(pre_hi, bw) : pre_hi;
+    left_store<T, MAXM>(LP, W, ldw, top, c, m, 0, keep_lo);
+    for (int idx = tid; idx < (pre_hi - keep_lo) * m; idx += nt) {
+        const int jj = keep_lo + idx / m, k = idx - (jj - keep_lo) * m;
+        RP[k * MAXM + (jj - bw)] = LP[jj * MAXM + k];
+    }
 
     // ---- tail: after the previous sweep's next row-bulge, straight from registers
     if (pre_hi <= ncols) {
@@ -301,9 +305,15 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
                 w += __shfl_xor_sync(FULL, w, 1);
                 const T a0 = __shfl_sync(FULL, act ? a[0] : (T)0, lane & ~1);   // row c (p = 0's first)
                 const T u = tauL * fma(vsL, w, a0);
+                if (carry_out && jj >= bw) {   // kept for the next row-bulge
 #pragma unroll
-                for (int i = 0; i < H; ++i)
-                    if (act && k0 + i < m) stcg(col + i, fma(-u, vL[k0 + i], a[i]));
+                    for (int i = 0; i < H; ++i)
+                        if (act && k0 + i < m) RP[(k0 + i) * MAXM + (jj - bw)] = fma(-u, vL[k0 + i], a[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < H; ++i)
+                        if (act && k0 + i < m) stcg(col + i, fma(-u, vL[k0 + i], a[i]));
+                }
             }
         }
     }
@@ -312,9 +322,10 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
 
 // One bandwidth-reduction stage (Algorithm 1, all sweeps) of every problem:
 // a persistent launch in which CTAs claim sweeps in order.  Sweep R may start
-// row-bulge s once sweep R-1 has finished row-bulge s (s+2 when the stage
-// ends at bandwidth 1), and its left panel's tail waits for row-bulge s+1 of
-// sweep R-1 (Section III-A separation of 2, resp. 3, row-bulges).
+// row-bulge s once sweep R-1 has finished row-bulge s (s+1 when the stage ends
+// at bandwidth 1), and its left panel's tail waits for the right half of
+// row-bulge s+1 (s+2) of sweep R-1: the Section III-A separation of 2 (3)
+// row-bulges, with the overlap the footprints allow.
 template <typename T, int MAXM>
 __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
 {
@@ -364,29 +375,62 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         T* W = (T*)L.wbase + D.w_off;
         const bool stall = (L.flags & BB_FLAG_INJECT_STALL) && stage == 0 && R == 0;
 
+        // Waits on sweep R-1 (progress values relative to the stage base):
+        //   split stage (bw - d >= 2): row-bulge s starts once row-bulge s of
+        //     R-1 is complete; the left panel's tail (offsets >= bw-1) once the
+        //     right half of row-bulge s+1 of R-1 is done (all of it when
+        //     bw - d == 2: there the left half of row-bulge s+1 of sweep R-2
+        //     reaches the tail rows too).
+        //   final stage (bw - d == 1): row-bulge s starts once row-bulge s+1 of
+        //     R-1 is complete; the tail is the last left-panel column (offset
+        //     d + bw), which only the right half of row-bulge s+2 of R-1 shares.
+        //   last row-bulge of the sweep: its completion is published only once
+        //     sweep R-1 is complete, so a completed sweep vouches for the whole
+        //     chain before it (a sweep can be one row-bulge shorter than R-1).
+        // The protocol is checked against every row-bulge's footprint on the
+        // host (serialisable: same result as the sequential sweep order).
+        const int pre_ahead = split ? 1 : 2;
+        const int tail_ahead = split ? 1 : 2;
+        const int tail_half = split ? (bw - d >= 3 ? 1 : 2) : 1;
+        const int tail_start = split ? bw - 1 : d + bw;
+        // From row-bulge 1 on, the bulge row and the rows below it up to c+m-1
+        // come from this CTA's previous row-bulge (kept in RP): warp 0 builds
+        // the right reflector from them while another thread waits on sweep R-1.
         bool ok = true;
+        bool carried = false;
         for (int s = 0; s < ns; ++s) {
-            if (tid == 0) {
+            if (carried && tid < 32) {
+                const int cs = R + (bw - d) + s * bw;
+                warp_reflector<T>(min(d + 1, n - cs), RP, tsR, vR, tb);
+            }
+            if (tid == (carried ? 32 : 0)) {
                 bool w_ok = true;
-                if (R > 0)   // row-bulge s (s+2 when not split) of sweep R-1 complete
-                    w_ok = wait_at_least(&prog[(R - 1) * ps],
-                                         base + 2 * min(s + (split ? 1 : 3), nsp), L.hdr, L.timeout_ns);
+                if (R > 0)
+                    w_ok = wait_at_least(&prog[(R - 1) * ps], base + 2 * min(s + pre_ahead, nsp),
+                                         L.hdr, L.timeout_ns);
                 s_ok = w_ok;
             }
             __syncthreads();
             if (!s_ok) { ok = false; break; }
+            const bool carry_out = s + 1 < ns;
             const bool step_ok = row_bulge<T, MAXM>(
                 D, W, bw, d, R, s, RP, LP, wbuf, tsR, tsL, vR, vL, tb, &s_tail_ok,
-                (split && R > 0) ? &prog[(R - 1) * ps] : nullptr,
-                // right half of row-bulge s+1 of sweep R-1 (or that sweep complete).
-                // With bw - d == 2 the left half of row-bulge s+1 of sweep R-2 reaches
-                // the tail rows too, so there the whole of row-bulge s+1 is awaited.
-                base + (s + 1 < nsp ? 2 * (s + 1) + (bw - d >= 3 ? 1 : 2) : 2 * nsp),
-                split ? bw - 1 : (1 << 30), L.hdr, L.timeout_ns,
-                stall ? nullptr : &prog[R * ps], base + 2 * s + 1);
+                R > 0 ? &prog[(R - 1) * ps] : nullptr,
+                base + (s + tail_ahead < nsp ? 2 * (s + tail_ahead) + tail_half : 2 * nsp),
+                tail_start, L.hdr, L.timeout_ns,
+                stall ? nullptr : &prog[R * ps], base + 2 * s + 1, carried, carry_out);
+            carried = carry_out;
             __syncthreads();
             if (!step_ok) { ok = false; break; }
-            if (tid == 0 && !stall) st_release(&prog[R * ps], base + 2 * s + 2);   // cumulative release
+            if (tid == 0) {
+                bool w_ok = true;
+                if (s == ns - 1 && R > 0)
+                    w_ok = wait_at_least(&prog[(R - 1) * ps], base + 2 * nsp, L.hdr, L.timeout_ns);
+                if (w_ok && !stall) st_release(&prog[R * ps], base + 2 * s + 2);   // cumulative
+                s_ok = w_ok;
+            }
+            __syncthreads();
+            if (!s_ok) { ok = false; break; }
         }
         if (!ok) break;
         if (tid == 0 && !stall && ns == 0) st_release(&prog[R * ps], base);
@@ -497,6 +541,8 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
         max_stages = std::max(max_stages, D.nstages);
         max_b = std::max(max_b, D.b);
     }
+    // progress words hold stage * PROG_STAGE + step marks in an int
+    if (max_stages >= INT32_MAX / PROG_STAGE) return BB_ERR_UNSUPPORTED;
     P->max_stages = max_stages;
     P->max_b = max_b;
     size_t off = 0;
@@ -556,8 +602,10 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
 {
     auto kern = bulge_kernel<T, MAXM>;
     if (P.smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) != cudaSuccess) {
+            cudaGetLastError();   // not sticky: leave no error for the caller's next launch
             return BB_ERR_UNSUPPORTED;
+        }
     }
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -576,8 +624,10 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
         const int tpb = stage_tpb(bw_max, d_max, P.tune.tpb);
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, P.smem) != cudaSuccess ||
-            per_sm < 1)
+            per_sm < 1) {
+            cudaGetLastError();
             return BB_ERR_UNSUPPORTED;
+        }
         int64_t grid = (int64_t)nsm * per_sm;
         if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
         grid = std::min<int64_t>(grid, L.total_tasks);
@@ -622,6 +672,12 @@ int launch_all_t(const LaunchPlan& P, cudaStream_t st)
 // enqueue: zero the counters, (upload the table), pack, bulge, extract
 int enqueue(LaunchPlan* P, void* ws, const void* host_descs, cudaStream_t st)
 {
+    // panels that cannot fit this device's shared memory: refuse before any work
+    int dev = 0, smem_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return BB_ERR_LAUNCH;
+    if (P->max_stages > 0 && P->smem > (size_t)smem_optin) return BB_ERR_UNSUPPORTED;
     bind_workspace(P, ws);
     if (cudaMemsetAsync(ws, 0, P->off_w, st) != cudaSuccess) return BB_ERR_LAUNCH;
     if (P->L.count > 1) {

@@ -21,6 +21,20 @@ constexpr int PROG_STAGE = 1 << 20;   // progress word = stage * PROG_STAGE + 2 
 template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
 
+// Asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes),
+// completed by cp_async_wait_all().  The data it reads was published by other
+// SMs through a release / acquire pair that one thread of the CTA observed
+// before a barrier, which orders these reads after it.
+template <typename T> __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
     int v;

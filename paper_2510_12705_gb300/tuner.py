@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-TWS = (8, 16, 32)
+TWS = (16, 32)             # TW = 8 (also in the paper's search) never won on GB300
 TPBS = (0, 256)            # 0: sized per stage (two threads per panel row + a reflector warp)
 SIFS = (0, 1)              # 0: as many resident sweeps as fit; 1: one per SM
 IN_DIM = 8
@@ -102,10 +102,14 @@ def collect(grid, reps: int = 1, log=None, out=None):
     return rows
 
 
-def default_grid(n_max: int = 16384, max_nb: int = 1 << 22):
+HELD_OUT = (65536, 256, "f32")
+
+
+def default_grid(n_max: int = 65536, max_nb: int = 1 << 23):
     """Training grid: n = 1024, 2048, ... n_max; b in {16, 32, ..., 512} with
-    b <= n/4 and n*b <= max_nb (the cost of one reduction grows like n*b);
-    FP32 and FP64."""
+    b <= n/4 and n*b <= max_nb (the cost of one reduction grows like n*b),
+    plus n = 65536, b = 256 in FP64; FP32 and FP64.  The held-out problem
+    n = 65536, b = 256, FP32 is never part of it."""
     grid = []
     n = 1024
     while n <= n_max:
@@ -114,7 +118,9 @@ def default_grid(n_max: int = 16384, max_nb: int = 1 << 22):
                 for dtype in ("f32", "f64"):
                     grid.append((n, b, dtype))
         n *= 2
-    return grid
+    if n_max >= 65536:
+        grid.append((65536, 256, "f64"))
+    return [g for g in grid if g != HELD_OUT]
 
 
 class MlpTuner:
@@ -245,7 +251,7 @@ def main(argv=None):
     c = sub.add_parser("collect")
     c.add_argument("--out", required=True)
     c.add_argument("--reps", type=int, default=1)
-    c.add_argument("--n-max", type=int, default=16384)
+    c.add_argument("--n-max", type=int, default=65536)
     t = sub.add_parser("train")
     t.add_argument("--data", required=True)
     t.add_argument("--out", required=True)

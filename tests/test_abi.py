@@ -125,6 +125,16 @@ def test_tuning_entry_points_host_checks(bb):
                          None) == bb.BB_ERR_ARG
 
 
+def test_stage_count_limit(bb):
+    # 2047 stages or more would overflow the int progress words: refused on the host
+    assert bb.band_to_bidiag_workspace_size(4096, 2047, bb.BB_F64, bb.Tuning(tw=1)) > 0
+    assert bb.band_to_bidiag_workspace_size(4096, 2048, bb.BB_F64, bb.Tuning(tw=1)) == 0
+    L = bb.lib()
+    t = bb.Tuning(tw=1)
+    assert L.band_to_bidiag_ex(4096, 2048, 1, 16, 2049, 16, 16, ctypes.byref(t), None, 0,
+                               None) == bb.BB_ERR_UNSUPPORTED
+
+
 def test_shared_bytes_model(bb):
     # both panels of a row-bulge: (MAXM + 1) x (b + TW + 2) elements each
     assert bb.bb_shared_bytes(4096, 128, bb.BB_F64, bb.Tuning(tw=16)) == 8 * 18 * 2 * (128 + 16 + 2)
@@ -140,8 +150,9 @@ def test_tuner_features_and_grid():
     f = tuner.features(65536, 256, "f32", c[0])
     assert len(f) == tuner.IN_DIM and all(abs(x) < 4 for x in f)
     g = tuner.default_grid()
-    assert all(b <= n // 4 and n * b <= (1 << 22) for n, b, _ in g)
-    assert (65536, 256, "f32") not in g
+    assert all(b <= n // 4 and (n * b <= (1 << 23) or (n, b) == (65536, 256)) for n, b, _ in g)
+    assert (65536, 256, "f32") not in g and (65536, 256, "f64") in g
+    assert len(set(g)) == len(g)
 
 
 def test_workspace_size_model(bb):
