@@ -34,7 +34,6 @@ METRIC = "band->bidiag effective GFLOP/s at n=32768, b=128 (FP64; FP32 form alon
 L2_FLUSH_BYTES = 256 << 20
 ORACLE_SAMPLE_STEPS = 600_000        # row-bulges of the first stage (~10-30 s of CPU work)
 REF_STEP_SAMPLE = 150_000            # per --impl reference step
-TUNER_MODEL = os.path.join(ROOT, "paper_2510_12705_gb300", "tuner_model.json")
 
 
 def _peaks_file():
@@ -137,15 +136,8 @@ def pick_tuning(bb, torch, dev, n, b, dtype_code):
     """Hyperparameters for the timed reduction: the learned tuner's pick (one
     forward pass of the trained MLP on this GPU, outside the timed region), or
     the library default when no trained model is present."""
-    t = bb.bb_default_tuning(n, b, dtype_code)
-    if not os.path.exists(TUNER_MODEL):
-        return t, "library default"
     from paper_2510_12705_gb300 import tuner
-    tw, tpb, sif = tuner.MlpTuner.load(TUNER_MODEL).predict(
-        n, b, "f64" if dtype_code == bb.BB_F64 else "f32")
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    return bb.Tuning(tw=tw, tpb=tpb, sweeps_in_flight=nsm if sif else 0,
-                     timeout_s=t.timeout_s), "learned tuner"
+    return tuner.tuning_for(n, b, "f64" if dtype_code == bb.BB_F64 else "f32", dev)
 
 
 def run_ours(args, rank, world):

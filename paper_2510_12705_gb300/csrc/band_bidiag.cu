@@ -210,41 +210,53 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
     }
     __syncthreads();
 
-    // ---- C: row updates
+    // ---- C: row updates.  C1: the panel rows c..c+m-1, which become the left
+    //      panel's first columns (and column c, the left reflector's input), by
+    //      the first worker pairs; their warps then signal warp 0 (named
+    //      barrier 2), which starts the left reflector at once.  C2: the rows
+    //      r0..c-1 back to the working band by all workers; after a workers-only
+    //      barrier (3) one lane of the last warp publishes the right half.
+    const int np = nwt >> 1, pi = wt >> 1;     // worker pairs, this thread's pair
+    const int ri_c = c - r0;                   // first panel row at or below c
+    const int c1_warps = (2 * min(m, np) + 31) >> 5;
+    T* tbL = tb + 4;
     if (warp == 0) {
-        for (int k = lane; k < m; k += 32)
-            stcg(W + (int64_t)(c + k) * ldw + (r0 - c - k + top), k == 0 ? tb[1] : (T)0);
+        bar_sync_n(2, 32 * (1 + c1_warps));
+        // ---- D: left reflector (warp 0) || column dot products (workers)
+        const ReflScale sc = reflector_scale<T>(m, LP, tsL);
+        bar_arrive(1, nt);
+        reflector_finish<T>(m, sc, vL, tbL);
     } else {
         const T tau = tb[0], vs = tb[2];
-        for (int ri = 1 + (wt >> 1); ri < nr; ri += nwt >> 1) {
-            const int r = r0 + ri;
+        for (int ri = ri_c + pi; ri < nr; ri += np) {             // C1 -> LP
             const T* row = RP + ri * MAXM + k0;
             const T u = tau * fma(vs, wbuf[ri], RP[ri * MAXM]);
-            if (r >= c) {          // shared block: left-panel column k, row r - c
+#pragma unroll
+            for (int i = 0; i < H; ++i)
+                if (k0 + i < m) LP[(k0 + i) * MAXM + (ri - ri_c)] = fma(-u, vR[k0 + i], row[i]);
+        }
+        if (warp <= c1_warps) bar_arrive(2, 32 * (1 + c1_warps));
+        for (int ri = pi; ri < ri_c; ri += np) {                   // C2 -> band
+            const int r = r0 + ri;
+            T* dst = W + (int64_t)(c + k0) * ldw + (r - c - k0 + top);   // (r, c+k0)
+            if (ri == 0) {            // the bulge row: (beta, 0, ..., 0)
 #pragma unroll
                 for (int i = 0; i < H; ++i)
-                    if (k0 + i < m) LP[(k0 + i) * MAXM + (r - c)] = fma(-u, vR[k0 + i], row[i]);
+                    if (k0 + i < m) stcg(dst + (int64_t)i * (ldw - 1), k0 + i == 0 ? tb[1] : (T)0);
             } else {
-                T* dst = W + (int64_t)(c + k0) * ldw + (r - c - k0 + top);   // (r, c+k0)
+                const T* row = RP + ri * MAXM + k0;
+                const T u = tau * fma(vs, wbuf[ri], RP[ri * MAXM]);
 #pragma unroll
                 for (int i = 0; i < H; ++i)
                     if (k0 + i < m) stcg(dst + (int64_t)i * (ldw - 1), fma(-u, vR[k0 + i], row[i]));
             }
         }
-    }
-    __syncthreads();
-
-    // the right reflector's results outside the left panel are in the working
-    // band: the next sweep's previous row-bulge may now finish its tail
-    if (tid == 0 && half_prog) st_release(half_prog, half_value);
-
-    // ---- D: left reflector (warp 0) || column dot products (workers)
-    T* tbL = tb + 4;
-    if (warp == 0) {
-        const ReflScale sc = reflector_scale<T>(m, LP, tsL);
-        bar_arrive(1, nt);
-        reflector_finish<T>(m, sc, vL, tbL);
-    } else {
+        bar_sync_n(3, nt - 32);
+        // the right reflector's results outside the left panel are in the
+        // working band: the next sweep's previous row-bulge may now finish its
+        // tail.  The release waits until the stores are performed; the last
+        // warp is idle in D unless the panel is very wide.
+        if (tid == nt - 32 && half_prog) st_release(half_prog, half_value);
         bar_sync_n(1, nt);
         for (int jj = 1 + (wt >> 1); jj - (wt >> 1) < pre_hi; jj += nwt >> 1) {
             T w = (T)0;
@@ -337,7 +349,7 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
     __shared__ int s_task[4];
     __shared__ int s_ok;         // result of the per-step wait
     __shared__ int s_tail_ok;    // result of the tail wait inside a row-bulge
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int stage = L.stage;
 
     for (;;) {
@@ -422,15 +434,23 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
             carried = carry_out;
             __syncthreads();
             if (!step_ok) { ok = false; break; }
-            if (tid == 0) {
-                bool w_ok = true;
-                if (s == ns - 1 && R > 0)
-                    w_ok = wait_at_least(&prog[(R - 1) * ps], base + 2 * nsp, L.hdr, L.timeout_ns);
-                if (w_ok && !stall) st_release(&prog[R * ps], base + 2 * s + 2);   // cumulative
-                s_ok = w_ok;
+            if (s == ns - 1) {
+                if (tid == 0) {
+                    bool w_ok = true;
+                    if (R > 0)
+                        w_ok = wait_at_least(&prog[(R - 1) * ps], base + 2 * nsp, L.hdr, L.timeout_ns);
+                    if (w_ok && !stall) st_release(&prog[R * ps], base + 2 * s + 2);   // cumulative
+                    s_ok = w_ok;
+                }
+                __syncthreads();
+                if (!s_ok) { ok = false; break; }
+            } else if (tid == nt - 32 && !stall) {
+                // completion of row-bulge s: issued by one lane of the last warp
+                // while warp 0 builds the next right reflector and thread 32
+                // waits on sweep R-1, so the release's wait for the stores is
+                // off their path (the barrier before the next loads orders it)
+                st_release(&prog[R * ps], base + 2 * s + 2);
             }
-            __syncthreads();
-            if (!s_ok) { ok = false; break; }
         }
         if (!ok) break;
         if (tid == 0 && !stall && ns == 0) st_release(&prog[R * ps], base);

@@ -27,6 +27,8 @@ def main(argv=None):
     ap.add_argument("--tw", type=int, default=0)
     ap.add_argument("--tpb", type=int, default=0)
     ap.add_argument("--sif", type=int, default=0)
+    ap.add_argument("--tuned", action="store_true",
+                    help="hyperparameters from the trained tuner (as bench.py uses them)")
     args = ap.parse_args(argv)
 
     import torch
@@ -41,7 +43,11 @@ def main(argv=None):
     band = torch.from_numpy(bandgen.random_band(args.n, args.b, seed=args.seed)).to("cuda", dt)
     d = torch.empty(args.n, device="cuda", dtype=dt)
     e = torch.empty(max(args.n - 1, 1), device="cuda", dtype=dt)
-    tun = bb.bb_default_tuning(args.n, args.b, code)
+    if args.tuned:
+        from paper_2510_12705_gb300 import tuner
+        tun, _ = tuner.tuning_for(args.n, args.b, args.dtype)
+    else:
+        tun = bb.bb_default_tuning(args.n, args.b, code)
     if args.tw:
         tun.tw = args.tw
     if args.tpb:
@@ -66,6 +72,7 @@ def main(argv=None):
     status = bb.bb_device_status(stream, reset=True)
     w = bb.bb_schedule_counts(args.n, args.b, tun.tw)
     print(json.dumps({"n": args.n, "b": args.b, "dtype": args.dtype, "tw": tun.tw, "tpb": tun.tpb,
+                      "sweeps_in_flight": tun.sweeps_in_flight,
                       "status": status, "flops": w.flops, "row_bulges": w.steps, "runs": out}))
     return 0 if status == 0 else 1
 

@@ -245,6 +245,26 @@ def evaluate(tuner: "MlpTuner", n: int, b: int, dtype: str, reps: int = 1) -> di
     return out
 
 
+MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuner_model.json")
+
+
+def tuning_for(n: int, b: int, dtype: str, device: int = 0):
+    """(Tuning, source) for a problem: the trained tuner's pick (one MLP
+    forward launch on the GPU) when the packaged model exists, else the
+    library default."""
+    import torch
+
+    import paper_2510_12705_gb300 as bb
+    code = bb.BB_F64 if dtype == "f64" else bb.BB_F32
+    t = bb.bb_default_tuning(n, b, code)
+    if not os.path.exists(MODEL_PATH):
+        return t, "library default"
+    tw, tpb, sif = MlpTuner.load(MODEL_PATH).predict(n, b, dtype)
+    nsm = torch.cuda.get_device_properties(device).multi_processor_count
+    return bb.Tuning(tw=tw, tpb=tpb, sweeps_in_flight=nsm if sif else 0,
+                     timeout_s=t.timeout_s), "learned tuner"
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)

@@ -164,15 +164,11 @@ def test_full_size_properties(full_size, dtype, tuning):
     # properties that hold at any size: d[0] = A[0,0]; |e[0]| = ||A[0,1:]||;
     # sum sigma^2 and sum sigma^4 preserved; the largest singular values.
     # "bench": the hyperparameters bench.py times (the learned tuner's pick)
-    import torch
-
-    import bench
-    import paper_2510_12705_gb300 as bb
+    from paper_2510_12705_gb300 import tuner
     ab, p1, p2, top = full_size
     tun = None
     if tuning == "bench":
-        code = bb.BB_F64 if dtype == "f64" else bb.BB_F32
-        tun, _ = bench.pick_tuning(bb, torch, 0, 32768, 128, code)
+        tun, _ = tuner.tuning_for(32768, 128, dtype)
     d, e, st = run_gpu(ab, 128, dtype, tuning=tun)
     assert st == 0
     a00 = ab[0, 128]
