@@ -220,11 +220,21 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
     const int ri_c = c - r0;                   // first panel row at or below c
     const int c1_warps = (2 * min(m, np) + 31) >> 5;
     T* tbL = tb + 4;
+    // The left panel's tail columns (offsets pre_hi..ncols) are loaded during D
+    // by the last warp, after the previous sweep's progress word says that its
+    // next row-bulge has done the part that touches them; with three or more
+    // warps that warp takes no part in D's dot products (named barrier 1 then
+    // counts the other threads).
+    const int nw = nt >> 5;
+    const bool has_tail = pre_hi <= ncols;
+    const bool tail_apart = has_tail && nw >= 3;
+    const int d_count = tail_apart ? nt - 32 : nt;
+    const int np_d = tail_apart ? np - 16 : np;
     if (warp == 0) {
         bar_sync_n(2, 32 * (1 + c1_warps));
         // ---- D: left reflector (warp 0) || column dot products (workers)
         const ReflScale sc = reflector_scale<T>(m, LP, tsL);
-        bar_arrive(1, nt);
+        bar_arrive(1, d_count);
         reflector_finish<T>(m, sc, vL, tbL);
     } else {
         const T tau = tb[0], vs = tb[2];
@@ -254,35 +264,69 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
         bar_sync_n(3, nt - 32);
         // the right reflector's results outside the left panel are in the
         // working band: the next sweep's previous row-bulge may now finish its
-        // tail.  The release waits until the stores are performed; the last
-        // warp is idle in D unless the panel is very wide.
+        // tail.  The release waits until the stores are performed, so it is
+        // issued from the last warp, not the reflector warp.
         if (tid == nt - 32 && half_prog) st_release(half_prog, half_value);
-        bar_sync_n(1, nt);
-        for (int jj = 1 + (wt >> 1); jj - (wt >> 1) < pre_hi; jj += nwt >> 1) {
-            T w = (T)0;
-            if (jj < pre_hi) {
-                const T* col = LP + jj * MAXM + k0;
-#pragma unroll
-                for (int i = 0; i < H; ++i)
-                    if (k0 + i >= 1 && k0 + i < m) w = fma(col[i], tsL[k0 + i], w);
+        if (has_tail && warp == nw - 1) {
+            // tail: wait (lane 0; the shuffle and __syncwarp order the other
+            // lanes' copies after its acquire), then copy the columns into LP
+            int t_ok = 1;
+            if (lane == 0 && tail_prog) t_ok = (int)wait_at_least(tail_prog, tail_target, hdr, timeout_ns);
+            t_ok = __shfl_sync(FULL, t_ok, 0);
+            __syncwarp();
+            if (t_ok) {
+                const float invM = 1.0f / (float)m;
+                for (int e = lane; e < (ncols + 1 - pre_hi) * m; e += 32) {
+                    const int q = fast_div(e, m, invM), k = e - q * m, jj = pre_hi + q;
+                    cp_async_elem(LP + jj * MAXM + k, W + (int64_t)(c + jj) * ldw + (top - jj + k));
+                }
+                cp_async_wait_all();
             }
-            w += __shfl_xor_sync(FULL, w, 1);
-            if (jj < pre_hi && p == 0) wbuf[jj] = w;
+            if (lane == 0) *s_flag = t_ok;
+        }
+        if (!(tail_apart && warp == nw - 1)) {
+            bar_sync_n(1, d_count);
+            for (int jj = 1 + pi; jj - pi < pre_hi; jj += np_d) {
+                T w = (T)0;
+                if (jj < pre_hi) {
+                    const T* col = LP + jj * MAXM + k0;
+#pragma unroll
+                    for (int i = 0; i < H; ++i)
+                        if (k0 + i >= 1 && k0 + i < m) w = fma(col[i], tsL[k0 + i], w);
+                }
+                w += __shfl_xor_sync(FULL, w, 1);
+                if (jj < pre_hi && p == 0) wbuf[jj] = w;
+            }
         }
     }
     __syncthreads();
+    if (has_tail && !*s_flag) return false;
 
-    // ---- E: column updates in LP, then coalesced stores
+    // ---- E: column updates in LP (the tail columns' dot products here too),
+    //      then stores.  Each pair reads its column into registers first and
+    //      shares the row-c entry by shuffle, so no lane overwrites an entry its
+    //      partner still has to read.
     const T tauL = tbL[0], vsL = tbL[2];
     if (warp == 0) {
         for (int k = lane; k < m; k += 32) LP[k] = k == 0 ? tbL[1] : (T)0;
     } else {
-        for (int jj = 1 + (wt >> 1); jj < pre_hi; jj += nwt >> 1) {
+        for (int jj = 1 + pi; jj - pi <= ncols; jj += np) {
+            const bool act = jj <= ncols;
             T* col = LP + jj * MAXM + k0;
-            const T u = tauL * fma(vsL, wbuf[jj], LP[jj * MAXM]);
+            T a[H];
+            T w = (T)0;
+#pragma unroll
+            for (int i = 0; i < H; ++i) {
+                a[i] = (act && k0 + i < m) ? col[i] : (T)0;
+                if (jj >= pre_hi && k0 + i >= 1 && k0 + i < m) w = fma(a[i], tsL[k0 + i], w);
+            }
+            w += __shfl_xor_sync(FULL, w, 1);
+            const T a0 = __shfl_sync(FULL, a[0], lane & ~1);
+            const T dot = (act && jj < pre_hi) ? wbuf[jj] : w;
+            const T u = tauL * fma(vsL, dot, a0);
 #pragma unroll
             for (int i = 0; i < H; ++i)
-                if (k0 + i < m) col[i] = fma(-u, vL[k0 + i], col[i]);
+                if (act && k0 + i < m) col[i] = fma(-u, vL[k0 + i], a[i]);
         }
     }
     __syncthreads();
@@ -290,44 +334,11 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
     // right panel rows 0..m-1 (its bulge row is row c): they stay in RP (free
     // since C) instead of a round trip through L2; the next row-bulge writes
     // them back in its phase C, before any other sweep may read them.
-    const int keep_lo = carry_out ? min(pre_hi, bw) : pre_hi;
+    const int keep_lo = carry_out ? min(bw, ncols + 1) : ncols + 1;
     left_store<T, MAXM>(LP, W, ldw, top, c, m, 0, keep_lo);
-    for (int idx = tid; idx < (pre_hi - keep_lo) * m; idx += nt) {
+    for (int idx = tid; idx < (ncols + 1 - keep_lo) * m; idx += nt) {
         const int jj = keep_lo + idx / m, k = idx - (jj - keep_lo) * m;
         RP[k * MAXM + (jj - bw)] = LP[jj * MAXM + k];
-    }
-
-    // ---- tail: after the previous sweep's next row-bulge, straight from registers
-    if (pre_hi <= ncols) {
-        if (tid == 0) *s_flag = tail_prog ? (int)wait_at_least(tail_prog, tail_target, hdr, timeout_ns) : 1;
-        __syncthreads();
-        if (!*s_flag) return false;
-        if (warp != 0) {
-            for (int jj = pre_hi + (wt >> 1); jj - (wt >> 1) <= ncols; jj += nwt >> 1) {
-                const bool act = jj <= ncols;
-                T* col = W + (int64_t)(c + jj) * ldw + (top - jj) + k0;   // row c+k0 of column c+jj
-                T a[H];
-                T w = (T)0;
-#pragma unroll
-                for (int i = 0; i < H; ++i)
-                    if (act && k0 + i < m) {
-                        a[i] = ldcg(col + i);
-                        if (k0 + i >= 1) w = fma(a[i], tsL[k0 + i], w);
-                    }
-                w += __shfl_xor_sync(FULL, w, 1);
-                const T a0 = __shfl_sync(FULL, act ? a[0] : (T)0, lane & ~1);   // row c (p = 0's first)
-                const T u = tauL * fma(vsL, w, a0);
-                if (carry_out && jj >= bw) {   // kept for the next row-bulge
-#pragma unroll
-                    for (int i = 0; i < H; ++i)
-                        if (act && k0 + i < m) RP[(k0 + i) * MAXM + (jj - bw)] = fma(-u, vL[k0 + i], a[i]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < H; ++i)
-                        if (act && k0 + i < m) stcg(col + i, fma(-u, vL[k0 + i], a[i]));
-                }
-            }
-        }
     }
     return true;
 }
