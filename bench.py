@@ -132,6 +132,19 @@ def run_reference(args, rank, world):
     return 0
 
 
+# DRAM bytes (read + write) per launch of the bulge kernel, from one ncu capture
+# of this workload (profiles/bulge_kernel_dram_n32768_b128.md), keyed by the
+# launch configuration; None (reported as null) for any other configuration.
+MEASURED_DRAM_BYTES_PER_LAUNCH = {
+    ("bulge_kernel<double,33>", 32768, 128, 32, 0, 0): 440363008.0,
+}
+
+
+def maxm_for(tw: int) -> int:
+    """Template size of the bulge kernel the library launches for this TW."""
+    return 5 if tw <= 4 else 9 if tw <= 8 else 17 if tw <= 16 else 33
+
+
 def pick_tuning(bb, torch, dev, n, b, dtype_code):
     """Hyperparameters for the timed reduction: the learned tuner's pick (one
     forward pass of the trained MLP on this GPU, outside the timed region), or
@@ -271,11 +284,14 @@ def run_ours(args, rank, world):
     achieved_l2_64 = bytes64 / (ms_kern * 1e-3) / 1e9              # GB/s
     achieved_l2_32 = bytes32 / (ms32_kern * 1e-3) / 1e9
     roofline = {
-        "bound": "alu", "kernel": "bulge_kernel<double,17>",
+        "bound": "alu", "kernel": f"bulge_kernel<double,{maxm_for(t64.tw)}>",
         "achieved": achieved_fp64 / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
         "frac": achieved_fp64 / fp64_peak if fp64_peak > 0 else None,
         "peak_source": "measured FP64 FMA rate on this GPU (bb_measure_fma_peak)",
-        "traffic": None,
+        "traffic": MEASURED_DRAM_BYTES_PER_LAUNCH.get(
+            (f"bulge_kernel<double,{maxm_for(t64.tw)}>", n, b, t64.tw, t64.tpb, t64.sweeps_in_flight)),
+        "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+        "algorithmic_bytes_per_launch": bytes64 / max(work64.stages, 1),
         "l2": {"achieved": achieved_l2_64, "peak": l2_gbs, "unit": "GB/s",
                "frac": achieved_l2_64 / l2_gbs if l2_gbs > 0 else None,
                "peak_source": "measured L2-resident copy bandwidth (bb_measure_l2_bandwidth)"},
