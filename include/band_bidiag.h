@@ -231,6 +231,23 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
                 float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * Singular values of the upper bidiagonal produced above (the third SVD
+ * stage, which the paper hands to LAPACK: Sections V-A and VII), on the GPU.
+ * bb_bidiag_sigma -- sigma_out[0..n-1] (device, FP64, descending) = the
+ * singular values of B = bidiag(d, e); d (n) and e (n-1) are device arrays of
+ * `dtype` (BB_F32 values are widened to FP64).  Method: one thread per
+ * singular value, bisection on the Sturm count of the Golub-Kahan matrix
+ * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...), to the
+ * resolution of FP64 around each value.  Cost O(n^2 log(1/eps)); asynchronous
+ * on `stream`.  workspace: device, >= bb_bidiag_sigma_workspace_size(n) bytes,
+ * 16-byte aligned.  Returns BB_OK, BB_ERR_ARG (n < 1, NULL pointers, dtype),
+ * BB_ERR_WORKSPACE, BB_ERR_UNSUPPORTED (n >= 2^31) or BB_ERR_LAUNCH.
+ */
+size_t bb_bidiag_sigma_workspace_size(int64_t n);
+int bb_bidiag_sigma(int64_t n, int dtype, const void *d, const void *e, double *sigma_out,
+                    void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * band_to_bidiag_noalloc -- the paper has no counterpart; this is a library
  * convenience.  Same contract as band_to_bidiag (default tuning), but the call
  * allocates no device memory: its scratch is a statically sized device array

@@ -91,6 +91,8 @@ def lib():
             "bb_measure_fma_peak": (ctypes.c_double, [ci, vp]),
             "bb_autotune": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, ci, ci,
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci), vp]),
+            "bb_bidiag_sigma_workspace_size": (sz, [i64]),
+            "bb_bidiag_sigma": (ci, [i64, ci, vp, vp, vp, vp, sz, vp]),
             "bb_mlp_param_count": (sz, [ci, ci]),
             "bb_mlp_backward_scratch": (sz, [ci, ci]),
             "bb_mlp_forward": (ci, [ci, ci, vp, vp, ci, vp, vp, vp, vp]),
@@ -350,3 +352,22 @@ def bb_mlp_adam(params, grads, m, v, step: int, lr: float, beta1: float = 0.9,
     rc = lib().bb_mlp_adam(params.numel(), params.data_ptr(), grads.data_ptr(), m.data_ptr(),
                            v.data_ptr(), step, lr, beta1, beta2, eps, _stream_handle(stream))
     _check(rc, "bb_mlp_adam")
+
+
+def bb_bidiag_sigma(d, e, sigma_out=None, workspace=None, stream=None):
+    """Singular values (FP64, descending, on the GPU) of the upper bidiagonal
+    with diagonal d (n) and superdiagonal e (n-1), CUDA tensors of one dtype."""
+    import torch
+    n = d.numel()
+    if e.dtype != d.dtype or (n > 1 and e.numel() < n - 1):
+        raise ValueError("d and e: one dtype, len(e) >= len(d) - 1")
+    if sigma_out is None:
+        sigma_out = torch.empty(n, dtype=torch.float64, device=d.device)
+    if workspace is None:
+        workspace = torch.empty(int(lib().bb_bidiag_sigma_workspace_size(n)), dtype=torch.uint8,
+                                device=d.device)
+    rc = lib().bb_bidiag_sigma(n, _dtype_code(d.dtype), d.data_ptr(), e.data_ptr() if n > 1 else None,
+                               sigma_out.data_ptr(), workspace.data_ptr(),
+                               workspace.numel() * workspace.element_size(), _stream_handle(stream))
+    _check(rc, "bb_bidiag_sigma")
+    return sigma_out

@@ -1,0 +1,171 @@
+// Singular values of the upper bidiagonal B = bidiag(d, e) on the GPU (the
+// third SVD stage that the paper leaves to LAPACK, Sections V-A and VII).
+//
+// The Golub-Kahan matrix T_GK (order 2n, zero diagonal, off-diagonal
+// f = (d0, e0, d1, e1, ..., d_{n-1})) has eigenvalues +-sigma_k.  For x > 0 its
+// Sturm count (negative pivots of the LDL^T factorisation of T_GK - x I,
+// q_0 = -x, q_i = -x - f_{i-1}^2 / q_{i-1}) equals n + #{sigma < x}.  Each
+// thread finds one singular value by bisection on [0, ub], ub a Gershgorin
+// bound, in FP64 whatever the storage type (the FP32 form's d, e are widened).
+// Reciprocals by Newton-Raphson from an FP32 start, two steps (full FP64); a
+// pivot that is (nearly) zero is replaced by -pivmin as in LAPACK's bisection.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "../../include/band_bidiag.h"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Bounds of the bisection, for the matrix scaled by the power of two sc that
+// brings the largest |f_i| into [1, 2) (exact; without it f_i^2 overflows for
+// entries above ~1e154): out = {ub, pivmin, sc, 1/sc} with
+// ub = sc * max_i (|f_{i-1}| + |f_i|) and pivmin = (sc * max |f_i|)^2 * DBL_MIN.
+// One block.
+template <typename T>
+__global__ void sigma_bounds_kernel(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
+                                    double* __restrict__ out)
+{
+    __shared__ double s_ub[32], s_fm[32];
+    double ub = 0.0, fm = 0.0;
+    const int64_t m = 2 * n - 1;   // number of off-diagonal entries of T_GK
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const double fi = (i & 1) ? (double)e[i >> 1] : (double)d[i >> 1];
+        const double fp = (i == 0) ? 0.0 : ((i & 1) ? (double)d[i >> 1] : (double)e[(i >> 1) - 1]);
+        ub = fmax(ub, 0.5 * fabs(fi) + 0.5 * fabs(fp));     // halved: no overflow near DBL_MAX
+        fm = fmax(fm, fabs(fi));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ub = fmax(ub, __shfl_xor_sync(FULL, ub, o));
+        fm = fmax(fm, __shfl_xor_sync(FULL, fm, o));
+    }
+    if ((threadIdx.x & 31) == 0) { s_ub[threadIdx.x >> 5] = ub; s_fm[threadIdx.x >> 5] = fm; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nw = blockDim.x >> 5;
+        ub = (threadIdx.x < nw) ? s_ub[threadIdx.x] : 0.0;
+        fm = (threadIdx.x < nw) ? s_fm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            ub = fmax(ub, __shfl_xor_sync(FULL, ub, o));
+            fm = fmax(fm, __shfl_xor_sync(FULL, fm, o));
+        }
+        if (threadIdx.x == 0) {
+            double sc = 1.0, isc = 1.0;
+            if (fm > 0.0) {
+                int ex = 0;
+                frexp(fm, &ex);                                    // fm = f 2^ex, f in [0.5, 1)
+                const int k = min(max(1 - ex, -1022), 1023);       // sc fm in [1, 2) unless subnormal
+                sc = ldexp(1.0, k);
+                isc = ldexp(1.0, -k);
+            }
+            const double fms = fm * sc;
+            out[0] = 2.0 * (ub * sc) * (1.0 + 4.0 * DBL_EPSILON) + DBL_MIN;   // strictly above sigma_max
+            out[1] = fmax(fms * fms * DBL_MIN, DBL_MIN);
+            out[2] = sc;
+            out[3] = isc;
+        }
+    }
+}
+
+// 1/x for a normal x of either sign, Newton-Raphson from the FP32 reciprocal
+// (two steps: ~2^-23 -> 2^-46 -> full precision).  |x| is kept inside the
+// FP32 range by the caller (|q| >= pivmin, and ub bounds the pivots above).
+__device__ __forceinline__ double rcp_newton(double x)
+{
+    const double ax = fabs(x);
+    // scale into [1, 2) so that the FP32 start neither overflows nor underflows
+    const int ex = ((int)((__double_as_longlong(ax) >> 52) & 0x7ff)) - 1023;
+    const double s = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex
+    const double xs = ax * s;
+    double y = (double)__frcp_rn((float)xs);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double r = fma(-xs, y, 1.0);
+        y = fma(y, r, y);
+    }
+    y *= s;
+    return x < 0.0 ? -y : y;
+}
+
+// #{sigma < x} for x > 0
+template <typename T>
+__device__ __forceinline__ int64_t count_below(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
+                                               double x, double pivmin, double sc)
+{
+    double q = -x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    int64_t neg = 1;   // q_0 < 0
+    for (int64_t k = 0; k < n; ++k) {
+        // f_{2k} = d_k, then f_{2k+1} = e_k (absent after d_{n-1})
+        const double dk = (double)__ldg(d + k) * sc;
+        q = fma(-dk * dk, rcp_newton(q), -x);
+        if (fabs(q) < pivmin) q = -pivmin;
+        neg += (q < 0.0);
+        if (k + 1 < n) {
+            const double ek = (double)__ldg(e + k) * sc;
+            q = fma(-ek * ek, rcp_newton(q), -x);
+            if (fabs(q) < pivmin) q = -pivmin;
+            neg += (q < 0.0);
+        }
+    }
+    return neg - n;
+}
+
+// thread j: the (j+1)-th smallest singular value, written to sigma[n-1-j]
+// (descending order, like LAPACK's xBDSQR)
+template <typename T>
+__global__ void sigma_bisect_kernel(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
+                                    const double* __restrict__ bounds, double* __restrict__ sigma)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double ub = bounds[0], pivmin = bounds[1], sc = bounds[2], isc = bounds[3];
+    double lo = 0.0, hi = ub;
+    // invariant: #{sigma < lo} <= j < #{sigma < hi}; stop at the resolution of
+    // the doubles around the answer (or after 200 halvings)
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin) break;
+        if (count_below(n, d, e, mid, pivmin, sc) > j) hi = mid; else lo = mid;
+    }
+    sigma[n - 1 - j] = (0.5 * (lo + hi)) * isc;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bb_bidiag_sigma_workspace_size(int64_t n)
+{
+    (void)n;
+    return 256;
+}
+
+int bb_bidiag_sigma(int64_t n, int dtype, const void* d, const void* e, double* sigma_out,
+                    void* workspace, size_t ws_bytes, void* stream)
+{
+    if (n < 1 || (dtype != BB_F32 && dtype != BB_F64) || !d || (n > 1 && !e) || !sigma_out)
+        return BB_ERR_ARG;
+    if (n >= ((int64_t)1 << 31)) return BB_ERR_UNSUPPORTED;
+    if (!workspace || ws_bytes < bb_bidiag_sigma_workspace_size(n) || ((uintptr_t)workspace & 15))
+        return BB_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* bounds = (double*)workspace;
+    // one warp per block: each thread is a long dependent FP64 chain, so
+    // spreading the values over all SMs beats packing warps onto a few
+    const unsigned grid = (unsigned)((n + 31) / 32);
+    if (dtype == BB_F64) {
+        sigma_bounds_kernel<double><<<1, 1024, 0, st>>>(n, (const double*)d, (const double*)e, bounds);
+        sigma_bisect_kernel<double><<<grid, 32, 0, st>>>(n, (const double*)d, (const double*)e, bounds, sigma_out);
+    } else {
+        sigma_bounds_kernel<float><<<1, 1024, 0, st>>>(n, (const float*)d, (const float*)e, bounds);
+        sigma_bisect_kernel<float><<<grid, 32, 0, st>>>(n, (const float*)d, (const float*)e, bounds, sigma_out);
+    }
+    return cudaGetLastError() == cudaSuccess ? BB_OK : BB_ERR_LAUNCH;
+}
+
+}  // extern "C"

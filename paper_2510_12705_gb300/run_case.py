@@ -27,6 +27,8 @@ def main(argv=None):
     ap.add_argument("--tw", type=int, default=0)
     ap.add_argument("--tpb", type=int, default=0)
     ap.add_argument("--sif", type=int, default=0)
+    ap.add_argument("--sigma", action="store_true",
+                    help="also time the singular values of the result on the GPU (bb_bidiag_sigma)")
     ap.add_argument("--tuned", action="store_true",
                     help="hyperparameters from the trained tuner (as bench.py uses them)")
     args = ap.parse_args(argv)
@@ -69,11 +71,24 @@ def main(argv=None):
         e1.record(stream)
         torch.cuda.synchronize()
         out.append({"kernel_ms": k0.elapsed_time(k1), "call_ms": e0.elapsed_time(e1)})
+    sig = None
+    if args.sigma:
+        s_out = torch.empty(args.n, device="cuda", dtype=torch.float64)
+        sws = torch.empty(int(bb.lib().bb_bidiag_sigma_workspace_size(args.n)), dtype=torch.uint8,
+                          device="cuda")
+        bb.bb_bidiag_sigma(d, e, s_out, sws, stream=stream)          # warm-up
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        bb.bb_bidiag_sigma(d, e, s_out, sws, stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sig = {"sigma_ms": s0.elapsed_time(s1), "sigma_max": float(s_out[0]), "sigma_min": float(s_out[-1])}
     status = bb.bb_device_status(stream, reset=True)
     w = bb.bb_schedule_counts(args.n, args.b, tun.tw)
     print(json.dumps({"n": args.n, "b": args.b, "dtype": args.dtype, "tw": tun.tw, "tpb": tun.tpb,
                       "sweeps_in_flight": tun.sweeps_in_flight,
-                      "status": status, "flops": w.flops, "row_bulges": w.steps, "runs": out}))
+                      "status": status, "flops": w.flops, "row_bulges": w.steps, "runs": out,
+                      "sigma": sig}))
     return 0 if status == 0 else 1
 
 

@@ -125,6 +125,20 @@ def test_tuning_entry_points_host_checks(bb):
                          None) == bb.BB_ERR_ARG
 
 
+def test_bidiag_sigma_host_checks(bb):
+    L = bb.lib()
+    ws = bb.lib().bb_bidiag_sigma_workspace_size(100)
+    assert ws >= 16
+    # validation happens before any CUDA call
+    assert L.bb_bidiag_sigma(0, 1, 16, 16, 16, 256, ws, None) == bb.BB_ERR_ARG
+    assert L.bb_bidiag_sigma(10, 7, 16, 16, 16, 256, ws, None) == bb.BB_ERR_ARG
+    assert L.bb_bidiag_sigma(10, 1, 16, None, 16, 256, ws, None) == bb.BB_ERR_ARG
+    assert L.bb_bidiag_sigma(10, 1, None, 16, 16, 256, ws, None) == bb.BB_ERR_ARG
+    assert L.bb_bidiag_sigma(10, 1, 16, 16, 16, None, ws, None) == bb.BB_ERR_WORKSPACE
+    assert L.bb_bidiag_sigma(10, 1, 16, 16, 16, 256, 8, None) == bb.BB_ERR_WORKSPACE
+    assert L.bb_bidiag_sigma(10, 1, 16, 16, 16, 257, ws, None) == bb.BB_ERR_WORKSPACE
+
+
 def test_stage_count_limit(bb):
     # 2047 stages or more would overflow the int progress words: refused on the host
     assert bb.band_to_bidiag_workspace_size(4096, 2047, bb.BB_F64, bb.Tuning(tw=1)) > 0
