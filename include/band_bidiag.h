@@ -237,8 +237,9 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
  * singular values of B = bidiag(d, e); d (n) and e (n-1) are device arrays of
  * `dtype` (BB_F32 values are widened to FP64).  Method: one thread per
  * singular value, bisection on the Sturm count of the Golub-Kahan matrix
- * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...), to the
- * resolution of FP64 around each value.  Cost O(n^2 log(1/eps)); asynchronous
+ * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...), to an
+ * absolute accuracy of about eps * sigma_max (the FP64 resolution for the
+ * largest values).  Cost O(n^2 log(1/eps)); asynchronous
  * on `stream`.  workspace: device, >= bb_bidiag_sigma_workspace_size(n) bytes,
  * 16-byte aligned.  Returns BB_OK, BB_ERR_ARG (n < 1, NULL pointers, dtype),
  * BB_ERR_WORKSPACE, BB_ERR_UNSUPPORTED (n >= 2^31) or BB_ERR_LAUNCH.

@@ -1,6 +1,6 @@
-// Microbenchmarks for the roofline denominators that the measured peak
-// file does not provide: L2-resident copy bandwidth and the FP32 / FP64 FMA
-// rates of the CUDA cores.  The bulge-chasing path keeps its working band in
+// Microbenchmarks for roofline denominators that a plain HBM copy and a bf16
+// GEMM do not give: L2-resident copy bandwidth and the FP32 / FP64 FMA rates
+// of the CUDA cores.  The bulge-chasing path keeps its working band in
 // L2 and, in FP64, is bounded by the FP64 pipe; both peaks are measured on the
 // GPU the library runs on.
 #include <cuda_runtime.h>

@@ -6,7 +6,9 @@
 // Sturm count (negative pivots of the LDL^T factorisation of T_GK - x I,
 // q_0 = -x, q_i = -x - f_{i-1}^2 / q_{i-1}) equals n + #{sigma < x}.  Each
 // thread finds one singular value by bisection on [0, ub], ub a Gershgorin
-// bound, in FP64 whatever the storage type (the FP32 form's d, e are widened).
+// bound, to the absolute accuracy eps * ub (relative accuracy for the values
+// near the top), in FP64 whatever the storage type (the FP32 form's d, e are
+// widened).
 // Reciprocals by Newton-Raphson from an FP32 start, two steps (full FP64); a
 // pivot that is (nearly) zero is replaced by -pivmin as in LAPACK's bisection.
 #include <cuda_runtime.h>
@@ -124,12 +126,15 @@ __global__ void sigma_bisect_kernel(int64_t n, const T* __restrict__ d, const T*
     if (j >= n) return;
     const double ub = bounds[0], pivmin = bounds[1], sc = bounds[2], isc = bounds[3];
     double lo = 0.0, hi = ub;
-    // invariant: #{sigma < lo} <= j < #{sigma < hi}; stop at the resolution of
-    // the doubles around the answer (or after 200 halvings)
+    // invariant: #{sigma < lo} <= j < #{sigma < hi}.  Stop at the FP64
+    // resolution around the value or at the absolute accuracy eps * ub (the
+    // accuracy of any backward-stable bidiagonal SVD, and what bisection can
+    // guarantee for values far below sigma_max): at most ~55 halvings
+    const double abs_tol = 0.5 * DBL_EPSILON * ub;
     for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin) break;
+        if (hi - lo <= fmax(2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)), abs_tol) + 2.0 * pivmin) break;
         if (count_below(n, d, e, mid, pivmin, sc) > j) hi = mid; else lo = mid;
     }
     sigma[n - 1 - j] = (0.5 * (lo + hi)) * isc;
