@@ -13,9 +13,11 @@
  *         A[i][j] = band[(b + i - j) + j * ldab]   for 0 <= j - i <= b,
  *     ldab >= b + 1.  Entries of the first b columns that lie above row 0
  *     are ignored.  The input band is never modified.
- *   - Element type: BB_F64 (double) or BB_F32 (float) for band, d and e.
- *     BB_F32 stores and updates in FP32 and generates every reflector
- *     (norm, beta, tau) in FP64 from the FP32 data (the precision split).
+ *   - Element type: BB_F64 (double), BB_F32 (float), BB_F16 (__half) or
+ *     BB_BF16 (__nv_bfloat16) for band, d and e.  BB_F32 stores and updates
+ *     in FP32 and generates every reflector (norm, beta, tau) in FP64 from the
+ *     FP32 data (the precision split).  BB_F16 / BB_BF16 keep the working
+ *     band in 16 bits and do everything else as BB_F32 does.
  *   - Device pointers: band, d_out (n elements), e_out (n-1 elements; may be
  *     NULL when n == 1) and workspace are CUDA device pointers on the
  *     current device; the caller owns them.  `stream` is a cudaStream_t
@@ -52,6 +54,12 @@ extern "C" {
 
 #define BB_F32 0
 #define BB_F64 1
+/* half-precision storage forms (band, working band and d, e in 16 bits;
+ * panels and arithmetic in FP32, reflector generation in FP64, as in the FP32
+ * form); entries and row norms must stay inside the storage type's range
+ * (FP16: 65504, subnormal below 6.1e-5) */
+#define BB_F16 2
+#define BB_BF16 3
 
 /* tuning flags */
 #define BB_FLAG_INJECT_STALL 0x100   /* fault injection for tests: sweep 0 never reports

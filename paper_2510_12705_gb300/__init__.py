@@ -36,6 +36,8 @@ BB_ERR_WORKSPACE = 6
 BB_ERR_UNSUPPORTED = 7
 BB_F32 = 0
 BB_F64 = 1
+BB_F16 = 2
+BB_BF16 = 3
 BB_FLAG_INJECT_STALL = 0x100
 
 _lib = None
@@ -130,6 +132,10 @@ def _dtype_code(t) -> int:
         return BB_F64
     if t == torch.float32:
         return BB_F32
+    if t == torch.float16:
+        return BB_F16
+    if t == torch.bfloat16:
+        return BB_BF16
     raise TypeError(f"unsupported dtype {t}")
 
 
@@ -191,7 +197,10 @@ def band_to_bidiag_host(band, b: int, tuning=None, stream=None, out=None):
     import numpy as np
     band = np.ascontiguousarray(band)
     n, ldab = band.shape
-    code = BB_F64 if band.dtype == np.float64 else BB_F32
+    code = {np.dtype(np.float64): BB_F64, np.dtype(np.float32): BB_F32,
+            np.dtype(np.float16): BB_F16}.get(band.dtype)
+    if code is None:
+        raise TypeError(f"unsupported dtype {band.dtype} (float64, float32, float16)")
     if out is None:
         d = np.empty(n, dtype=band.dtype)
         e = np.empty(max(n - 1, 1), dtype=band.dtype)

@@ -35,6 +35,12 @@ static __device__ unsigned int g_bb_status;   // sticky device status (bits 1 <<
 
 // ------------------------------------------------------------------ kernels
 
+template <typename T> __device__ __forceinline__ bool finite_val(T v)
+{
+    if constexpr (sizeof(T) >= 4) return isfinite(v);
+    else return isfinite(to_float(v));
+}
+
 template <typename T>
 __global__ void pack_kernel(Launch L)
 {
@@ -54,7 +60,7 @@ __global__ void pack_kernel(Launch L)
             T v = (T)0;
             if (i >= 0 && k >= 0 && k <= D.b) {
                 v = bcol[D.b_in - k];
-                bad |= !isfinite(v);
+                bad |= !finite_val(v);
             }
             wcol[off] = v;
         }
@@ -114,14 +120,14 @@ __device__ __forceinline__ int fast_div(int e, int div, float inv)
 // left-panel columns jj in [lo, hi) back to the working band (exact rows):
 // element e of the block goes to row e mod m of column lo + e / m, so
 // consecutive threads write consecutive rows of a column
-template <typename T, int MAXM>
-__device__ __forceinline__ void left_store(const T* LP, T* __restrict__ W, int ldw, int top, int c,
+template <typename TS, typename T, int MAXM>
+__device__ __forceinline__ void left_store(const T* LP, TS* __restrict__ W, int ldw, int top, int c,
                                            int m, int lo, int hi)
 {
     const float invM = 1.0f / (float)m;
     for (int e = threadIdx.x; e < (hi - lo) * m; e += blockDim.x) {
         const int q = fast_div(e, m, invM), k = e - q * m, jj = lo + q;
-        stcg(W + (int64_t)(c + jj) * ldw + (top - jj + k), LP[jj * MAXM + k]);
+        panel_to_band<TS, T>(W + (int64_t)(c + jj) * ldw + (top - jj + k), LP[jj * MAXM + k]);
     }
 }
 
@@ -143,8 +149,8 @@ __device__ __forceinline__ void left_store(const T* LP, T* __restrict__ W, int l
 // (tail_prog >= tail_target) and updated straight from registers.  This
 // row-bulge publishes its own right half (half_prog = half_value) after C.
 // Returns false when a wait gave up.
-template <typename T, int MAXM>
-__device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int bw, int d, int R,
+template <typename TS, typename T, int MAXM>
+__device__ __forceinline__ bool row_bulge(const Desc& D, TS* __restrict__ W, int bw, int d, int R,
                                           int s, T* RP, T* LP, T* wbuf, T* tsR, T* tsL, T* vR, T* vL,
                                           T* tb, int* s_flag, const int* tail_prog, int tail_target,
                                           int tail_start, Header* hdr, unsigned long long timeout_ns,
@@ -175,11 +181,11 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
         for (int e = tid; e < tot; e += nt) {
             if (e < totR) {
                 const int k = fast_div(e, nrl, invR), ri = ri_lo + e - k * nrl;
-                cp_async_elem(RP + ri * MAXM + k, W + (int64_t)(c + k) * ldw + (r0 + ri - c - k + top));
+                band_to_panel<TS, T>(RP + ri * MAXM + k, W + (int64_t)(c + k) * ldw + (r0 + ri - c - k + top));
             } else {
                 const int f = e - totR;
                 const int q = fast_div(f, m, invM), k = f - q * m, jj = m + q;
-                cp_async_elem(LP + jj * MAXM + k, W + (int64_t)(c + jj) * ldw + (top - jj + k));
+                band_to_panel<TS, T>(LP + jj * MAXM + k, W + (int64_t)(c + jj) * ldw + (top - jj + k));
             }
         }
         cp_async_wait_all();
@@ -248,17 +254,17 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
         if (warp <= c1_warps) bar_arrive(2, 32 * (1 + c1_warps));
         for (int ri = pi; ri < ri_c; ri += np) {                   // C2 -> band
             const int r = r0 + ri;
-            T* dst = W + (int64_t)(c + k0) * ldw + (r - c - k0 + top);   // (r, c+k0)
+            TS* dst = W + (int64_t)(c + k0) * ldw + (r - c - k0 + top);   // (r, c+k0)
             if (ri == 0) {            // the bulge row: (beta, 0, ..., 0)
 #pragma unroll
                 for (int i = 0; i < H; ++i)
-                    if (k0 + i < m) stcg(dst + (int64_t)i * (ldw - 1), k0 + i == 0 ? tb[1] : (T)0);
+                    if (k0 + i < m) panel_to_band<TS, T>(dst + (int64_t)i * (ldw - 1), k0 + i == 0 ? tb[1] : (T)0);
             } else {
                 const T* row = RP + ri * MAXM + k0;
                 const T u = tau * fma(vs, wbuf[ri], RP[ri * MAXM]);
 #pragma unroll
                 for (int i = 0; i < H; ++i)
-                    if (k0 + i < m) stcg(dst + (int64_t)i * (ldw - 1), fma(-u, vR[k0 + i], row[i]));
+                    if (k0 + i < m) panel_to_band<TS, T>(dst + (int64_t)i * (ldw - 1), fma(-u, vR[k0 + i], row[i]));
             }
         }
         bar_sync_n(3, nt - 32);
@@ -278,7 +284,7 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
                 const float invM = 1.0f / (float)m;
                 for (int e = lane; e < (ncols + 1 - pre_hi) * m; e += 32) {
                     const int q = fast_div(e, m, invM), k = e - q * m, jj = pre_hi + q;
-                    cp_async_elem(LP + jj * MAXM + k, W + (int64_t)(c + jj) * ldw + (top - jj + k));
+                    band_to_panel<TS, T>(LP + jj * MAXM + k, W + (int64_t)(c + jj) * ldw + (top - jj + k));
                 }
                 cp_async_wait_all();
             }
@@ -335,7 +341,7 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
     // since C) instead of a round trip through L2; the next row-bulge writes
     // them back in its phase C, before any other sweep may read them.
     const int keep_lo = carry_out ? min(bw, ncols + 1) : ncols + 1;
-    left_store<T, MAXM>(LP, W, ldw, top, c, m, 0, keep_lo);
+    left_store<TS, T, MAXM>(LP, W, ldw, top, c, m, 0, keep_lo);
     for (int idx = tid; idx < (ncols + 1 - keep_lo) * m; idx += nt) {
         const int jj = keep_lo + idx / m, k = idx - (jj - keep_lo) * m;
         RP[k * MAXM + (jj - bw)] = LP[jj * MAXM + k];
@@ -349,7 +355,7 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, T* __restrict__ W, int 
 // at bandwidth 1), and its left panel's tail waits for the right half of
 // row-bulge s+1 (s+2) of sweep R-1: the Section III-A separation of 2 (3)
 // row-bulges, with the overlap the footprints allow.
-template <typename T, int MAXM>
+template <typename TS, typename T, int MAXM>
 __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         const int ps = L.prog_stride;
         const int ns = sweep_steps(n, bw, d, R);
         const int nsp = (R > 0) ? sweep_steps(n, bw, d, R - 1) : 0;
-        T* W = (T*)L.wbase + D.w_off;
+        TS* W = (TS*)L.wbase + D.w_off;
         const bool stall = (L.flags & BB_FLAG_INJECT_STALL) && stage == 0 && R == 0;
 
         // Waits on sweep R-1 (progress values relative to the stage base):
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
             __syncthreads();
             if (!s_ok) { ok = false; break; }
             const bool carry_out = s + 1 < ns;
-            const bool step_ok = row_bulge<T, MAXM>(
+            const bool step_ok = row_bulge<TS, T, MAXM>(
                 D, W, bw, d, R, s, RP, LP, wbuf, tsR, tsL, vR, vL, tb, &s_tail_ok,
                 R > 0 ? &prog[(R - 1) * ps] : nullptr,
                 base + (s + tail_ahead < nsp ? 2 * (s + tail_ahead) + tail_half : 2 * nsp),
@@ -476,6 +482,9 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 
 int clamp_b(int64_t n, int64_t b) { return (int)std::min<int64_t>(b, std::max<int64_t>(n - 1, 0)); }
+
+bool dtype_ok(int dtype) { return dtype == BB_F32 || dtype == BB_F64 || dtype == BB_F16 || dtype == BB_BF16; }
+int storage_size(int dtype) { return dtype == BB_F64 ? 8 : dtype == BB_F32 ? 4 : 2; }
 
 int num_stages(int b, int tw)
 {
@@ -531,7 +540,7 @@ struct LaunchPlan {
 int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* tuning,
                 LaunchPlan* P)
 {
-    if (count < 1 || !probs || (dtype != BB_F32 && dtype != BB_F64)) return BB_ERR_ARG;
+    if (count < 1 || !probs || !dtype_ok(dtype)) return BB_ERR_ARG;
     int64_t nmax = 0, bmax = 0;
     for (int q = 0; q < count; ++q) {
         const bb_problem& p = probs[q];
@@ -543,7 +552,7 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
     }
     if (!resolve_tuning(nmax, bmax, dtype, tuning, &P->tune)) return BB_ERR_ARG;
     const int tw = P->tune.tw;
-    P->esize = dtype == BB_F64 ? 8 : 4;
+    P->esize = storage_size(dtype);
     P->descs.resize(count);
     int64_t sweep_prefix = 0, col_prefix = 0, welems = 0;
     int max_stages = 0, max_b = 0;
@@ -604,7 +613,8 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
     L.rp_rows = max_b + tw + 2;
     L.lp_cols = max_b + tw + 2;
     L.stage = 0;
-    P->smem = (size_t)P->esize * ((size_t)maxm_for(tw) + 1) * (size_t)(L.rp_rows + L.lp_cols);
+    // panels hold the compute type: FP64 for the FP64 form, FP32 otherwise
+    P->smem = (size_t)(dtype == BB_F64 ? 8 : 4) * ((size_t)maxm_for(tw) + 1) * (size_t)(L.rp_rows + L.lp_cols);
     if (L.total_tasks >= (int64_t)INT32_MAX) return BB_ERR_UNSUPPORTED;
     return BB_OK;
 }
@@ -628,10 +638,10 @@ int stage_tpb(int bw, int d, int user_tpb)
     return std::max(96, std::min(512, t));
 }
 
-template <typename T, int MAXM>
+template <typename TS, typename T, int MAXM>
 int launch_stages(const LaunchPlan& P, cudaStream_t st)
 {
-    auto kern = bulge_kernel<T, MAXM>;
+    auto kern = bulge_kernel<TS, T, MAXM>;
     if (P.smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) != cudaSuccess) {
             cudaGetLastError();   // not sticky: leave no error for the caller's next launch
@@ -674,7 +684,7 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
     return BB_OK;
 }
 
-template <typename T>
+template <typename TS, typename T>
 int launch_all_t(const LaunchPlan& P, cudaStream_t st)
 {
     int dev = 0, nsm = 0;
@@ -682,21 +692,21 @@ int launch_all_t(const LaunchPlan& P, cudaStream_t st)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const unsigned cols_grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((P.L.total_cols + 7) / 8, (int64_t)nsm * 16));
-    pack_kernel<T><<<cols_grid, 256, 0, st>>>(P.L);
+    pack_kernel<TS><<<cols_grid, 256, 0, st>>>(P.L);
     if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
     if (P.max_stages > 0) {
         int rc;
         switch (maxm_for(P.tune.tw)) {
-            case 5: rc = launch_stages<T, 5>(P, st); break;
-            case 9: rc = launch_stages<T, 9>(P, st); break;
-            case 17: rc = launch_stages<T, 17>(P, st); break;
-            default: rc = launch_stages<T, 33>(P, st); break;
+            case 5: rc = launch_stages<TS, T, 5>(P, st); break;
+            case 9: rc = launch_stages<TS, T, 9>(P, st); break;
+            case 17: rc = launch_stages<TS, T, 17>(P, st); break;
+            default: rc = launch_stages<TS, T, 33>(P, st); break;
         }
         if (rc != BB_OK) return rc;
     }
     const unsigned ex_grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((P.L.total_cols + 255) / 256, (int64_t)nsm * 8));
-    extract_kernel<T><<<ex_grid, 256, 0, st>>>(P.L);
+    extract_kernel<TS><<<ex_grid, 256, 0, st>>>(P.L);
     return cudaGetLastError() == cudaSuccess ? BB_OK : BB_ERR_LAUNCH;
 }
 
@@ -716,7 +726,12 @@ int enqueue(LaunchPlan* P, void* ws, const void* host_descs, cudaStream_t st)
                             cudaMemcpyHostToDevice, st) != cudaSuccess)
             return BB_ERR_LAUNCH;
     }
-    return P->esize == 8 ? launch_all_t<double>(*P, st) : launch_all_t<float>(*P, st);
+    switch (P->tune.dtype) {
+        case BB_F64: return launch_all_t<double, double>(*P, st);
+        case BB_F32: return launch_all_t<float, float>(*P, st);
+        case BB_F16: return launch_all_t<__half, float>(*P, st);
+        default: return launch_all_t<__nv_bfloat16, float>(*P, st);
+    }
 }
 
 }  // namespace
@@ -729,7 +744,7 @@ int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning* out)
 {
     if (!out) return BB_ERR_ARG;
     (void)n;
-    out->tw = dtype == BB_F32 ? 32 : 16;     // one 128-byte line of the element type
+    out->tw = dtype == BB_F64 ? 16 : 32;     // one 128-byte line of FP64 / FP32 (the kernel's widest TW for half storage)
     out->tpb = 0;                             // per stage: two threads per panel row / column
     out->sweeps_in_flight = 0;
     out->flags = 0;
@@ -814,8 +829,8 @@ int band_to_bidiag_host(int64_t n, int64_t b, int dtype, const void* band, int64
                         void* d_out, void* e_out, const bb_tuning* tuning, void* stream)
 {
     if (!band || !d_out || (n > 1 && !e_out) || n < 1 || ldab < b + 1) return BB_ERR_ARG;
-    if (dtype != BB_F32 && dtype != BB_F64) return BB_ERR_ARG;
-    const size_t es = dtype == BB_F64 ? 8 : 4;
+    if (!dtype_ok(dtype)) return BB_ERR_ARG;
+    const size_t es = (size_t)storage_size(dtype);
     const size_t band_bytes = align_up(es * (size_t)ldab * (size_t)n);
     const size_t d_bytes = align_up(es * (size_t)n);
     const size_t ws_bytes = band_to_bidiag_workspace_size(n, b, dtype, tuning);

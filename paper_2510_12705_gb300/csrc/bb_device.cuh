@@ -10,6 +10,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace bb {
@@ -34,6 +36,32 @@ template <typename T> __device__ __forceinline__ void cp_async_elem(T* smem, con
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Storage type TS of the working band and compute type T of the panels: equal
+// for the FP64 and FP32 forms; FP16 / BF16 storage computes in FP32.
+template <typename T> __device__ __forceinline__ float to_float(T v) { return (float)v; }
+template <> __device__ __forceinline__ float to_float<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename TS, typename T> __device__ __forceinline__ TS to_storage(T v) { return (TS)v; }
+template <> __device__ __forceinline__ __half to_storage<__half, float>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16, float>(float v)
+{
+    return __float2bfloat16_rn(v);
+}
+
+// one element of the working band (L2, bypassing L1) into a panel: an
+// asynchronous copy when no conversion is needed, else a load and a convert
+template <typename TS, typename T> __device__ __forceinline__ void band_to_panel(T* smem, const TS* g)
+{
+    if constexpr (sizeof(TS) == sizeof(T)) cp_async_elem(smem, (const T*)g);
+    else *smem = (T)to_float(__ldcg(g));
+}
+template <typename TS, typename T> __device__ __forceinline__ void panel_to_band(TS* g, T v)
+{
+    if constexpr (sizeof(TS) == sizeof(T)) __stcg((T*)g, v);
+    else __stcg(g, to_storage<TS, T>(v));
+}
 
 __device__ __forceinline__ int ld_acquire(const int* p)
 {

@@ -139,6 +139,17 @@ def test_bidiag_sigma_host_checks(bb):
     assert L.bb_bidiag_sigma(10, 1, 16, 16, 16, 257, ws, None) == bb.BB_ERR_WORKSPACE
 
 
+def test_half_storage_host_model(bb):
+    # 16-bit working band, FP32 panels in shared memory
+    t = bb.Tuning(tw=32)
+    w16 = bb.band_to_bidiag_workspace_size(4096, 128, bb.BB_F16, t)
+    w32 = bb.band_to_bidiag_workspace_size(4096, 128, bb.BB_F32, t)
+    assert 0 < w16 < w32
+    assert bb.bb_shared_bytes(4096, 128, bb.BB_BF16, t) == bb.bb_shared_bytes(4096, 128, bb.BB_F32, t)
+    assert bb.bb_default_tuning(4096, 128, bb.BB_F16).tw == 32
+    assert bb.band_to_bidiag_workspace_size(4096, 128, 4, t) == 0      # unknown dtype
+
+
 def test_stage_count_limit(bb):
     # 2047 stages or more would overflow the int progress words: refused on the host
     assert bb.band_to_bidiag_workspace_size(4096, 2047, bb.BB_F64, bb.Tuning(tw=1)) > 0

@@ -102,3 +102,27 @@ def test_batch_plan_rejects_bad_problem():
     e = torch.empty(9, device="cuda", dtype=torch.float64)
     with pytest.raises(bb.BBError):
         bb.BatchPlan([(band, 5, d, e)])        # ldab = 3 < b + 1
+
+
+def test_shard_run_local_matches_single_calls():
+    """One rank's share of a partitioned batch (shard.run_local) gives the same
+    bits as reducing each of its problems alone."""
+    import torch
+
+    import paper_2510_12705_gb300 as bb
+    from paper_2510_12705_gb300 import shard
+    specs = [(300, 8, 1), (513, 16, 2), (128, 32, 3), (777, 5, 4), (64, 63, 5), (1000, 12, 6)]
+    problems = [(bandgen.random_band(n, b, seed=s), b) for n, b, s in specs]
+    parts = shard.partition([(ab.shape[0], b) for ab, b in problems], 2)
+    for rank in range(2):
+        got = shard.run_local(problems, parts[rank], dtype="f64")
+        assert sorted(got) == parts[rank]
+        for i in parts[rank]:
+            ab, b = problems[i]
+            band = torch.from_numpy(ab).cuda()
+            n = ab.shape[0]
+            d = torch.empty(n, device="cuda", dtype=torch.float64)
+            e = torch.empty(n - 1, device="cuda", dtype=torch.float64)
+            bb.band_to_bidiag(band, b, d, e)
+            assert np.array_equal(got[i][0], d.cpu().numpy())
+            assert np.array_equal(got[i][1], e.cpu().numpy())
