@@ -243,7 +243,8 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
  * stage, which the paper hands to LAPACK: Sections V-A and VII), on the GPU.
  * bb_bidiag_sigma -- sigma_out[0..n-1] (device, FP64, descending) = the
  * singular values of B = bidiag(d, e); d (n) and e (n-1) are device arrays of
- * `dtype` (BB_F32 values are widened to FP64).  Method: one thread per
+ * `dtype` BB_F64 or BB_F32 (widened to FP64; 16-bit outputs are converted by
+ * the caller first).  Method: one thread per
  * singular value, bisection on the Sturm count of the Golub-Kahan matrix
  * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...), to an
  * absolute accuracy of about eps * sigma_max (the FP64 resolution for the
