@@ -104,10 +104,27 @@ def oracle_sample(n, b, tw, max_steps, seed=SEED):
     return cnt["flops"], dt, cnt["steps"]
 
 
+def reference_tw(n: int, b: int) -> int:
+    """TW of our arm's FP64 configuration without touching the GPU path: the
+    committed tuner weights evaluated by the FP64 MLP oracle (the library's own
+    pick runs the same network with its GPU kernels); 16 without a model."""
+    from paper_2510_12705_gb300 import tuner
+    if not os.path.exists(tuner.MODEL_PATH):
+        return 16
+    import oracle.mlp as omlp
+    with open(tuner.MODEL_PATH) as f:
+        m = json.load(f)
+    cands = [tuple(c) for c in m["candidates"]]
+    X = np.array([tuner.features(n, b, "f64", c) for c in cands])
+    y, _, _ = omlp.forward(np.array(m["params"], np.float64), X, m["in_dim"], m["hidden"])
+    return cands[int(np.argmin(y))][0]
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    n, b, tw = args.n, args.b, 16
+    n, b = args.n, args.b
+    tw = reference_tw(n, b)
     ms, gf = [], []
     for i in range(args.warmup + args.steps):
         flops, dt, steps = oracle_sample(n, b, tw, REF_STEP_SAMPLE)
