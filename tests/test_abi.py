@@ -187,3 +187,31 @@ def test_workspace_size_model(bb):
     ldw = -(-(b + 2 * 16) // 4) * 4 + 1          # ldw - 1 a multiple of 4 (16-byte phase)
     assert ldw >= b + 2 * 16 + 1
     assert ldw * n * 8 <= ws <= ldw * n * 8 + 128 * n + 4096
+
+
+def test_committed_tuner_artifacts_consistent():
+    """The packaged model matches the tuner's feature set and candidates, its
+    timings file covers the training grid (held-out problem excluded), and the
+    FP64 MLP oracle evaluates the weights to the pick the bench's reference arm
+    uses."""
+    import json
+    import os
+
+    import bench
+    from paper_2510_12705_gb300 import tuner
+    if not os.path.exists(tuner.MODEL_PATH):
+        import pytest
+        pytest.skip("no trained tuner model")
+    with open(tuner.MODEL_PATH) as f:
+        m = json.load(f)
+    assert m["in_dim"] == tuner.IN_DIM and [tuple(c) for c in m["candidates"]] == tuner.candidates()
+    D, H = m["in_dim"], m["hidden"]
+    assert len(m["params"]) == H * D + H + H * H + H + H + 1
+    timings = os.path.join(os.path.dirname(tuner.MODEL_PATH), "tuner_timings.json")
+    with open(timings) as f:
+        rows = json.load(f)
+    probs = {(r["n"], r["b"], r["dtype"]) for r in rows}
+    assert tuner.HELD_OUT not in probs
+    assert probs <= set(tuner.default_grid())
+    assert all(r["ms"] > 0 for r in rows)
+    assert bench.reference_tw(32768, 128) in tuner.TWS
