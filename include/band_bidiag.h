@@ -246,7 +246,8 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
  * `dtype` BB_F64 or BB_F32 (widened to FP64; 16-bit outputs are converted by
  * the caller first).  Method: one thread per
  * singular value, bisection on the Sturm count of the Golub-Kahan matrix
- * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...), to an
+ * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...; three-term
+ * recurrence without divisions, restarted at splits), to an
  * absolute accuracy of about eps * sigma_max (the FP64 resolution for the
  * largest values).  Cost O(n^2 log(1/eps)); asynchronous
  * on `stream`.  workspace: device, >= bb_bidiag_sigma_workspace_size(n) bytes,

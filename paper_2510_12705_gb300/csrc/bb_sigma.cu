@@ -9,8 +9,8 @@
 // bound, to the absolute accuracy eps * ub (relative accuracy for the values
 // near the top), in FP64 whatever the storage type (the FP32 form's d, e are
 // widened).
-// Reciprocals by Newton-Raphson from an FP32 start, two steps (full FP64); a
-// pivot that is (nearly) zero is replaced by -pivmin as in LAPACK's bisection.
+// The count runs the three-term Sturm recurrence: no divisions, exact
+// power-of-two rescaling, restarts at splits, LAPACK's zero-pivot rule.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -72,46 +72,59 @@ __global__ void sigma_bounds_kernel(int64_t n, const T* __restrict__ d, const T*
     }
 }
 
-// 1/x for a normal x of either sign, Newton-Raphson from the FP32 reciprocal
-// (two steps: ~2^-23 -> 2^-46 -> full precision).  |x| is kept inside the
-// FP32 range by the caller (|q| >= pivmin, and ub bounds the pivots above).
-__device__ __forceinline__ double rcp_newton(double x)
+// #{sigma < x} for x > 0: the sign changes of the Sturm sequence p_0 = 1,
+// p_1 = -x, p_i = -x p_{i-1} - f_{i-1}^2 p_{i-2} (the LDL^T pivots are
+// q_i = p_i / p_{i-1}; a sign change is a negative pivot).  In this form a
+// pivot costs one FMA on the dependent chain and no division.
+//   - f_{i-1}^2 == 0 splits the matrix: the sequence restarts (q_i = -x < 0);
+//   - an exactly zero p_i is replaced by -pivmin p_{i-1} (the pivot rule of
+//     LAPACK's bisection; an underflow to a signed zero keeps the sign);
+//   - the pair (p_{i-1}, p_i) is rescaled by an exact power of two after every
+//     second pivot pair when its exponent leaves [-400, 400] (a pivot changes
+//     the magnitude by less than 16 for the scaled matrix).
+__device__ __forceinline__ void sturm_step(double& pm1, double& p, double f2, double x, double pivmin,
+                                           int64_t& neg)
 {
-    const double ax = fabs(x);
-    // scale into [1, 2) so that the FP32 start neither overflows nor underflows
-    const int ex = ((int)((__double_as_longlong(ax) >> 52) & 0x7ff)) - 1023;
-    const double s = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex
-    const double xs = ax * s;
-    double y = (double)__frcp_rn((float)xs);
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const double r = fma(-xs, y, 1.0);
-        y = fma(y, r, y);
+    if (f2 == 0.0) {
+        pm1 = 1.0;
+        p = -x;
+        neg += 1;
+        return;
     }
-    y *= s;
-    return x < 0.0 ? -y : y;
+    double pn = fma(-x, p, -(f2 * pm1));
+    if (pn == 0.0) pn = (p != 0.0) ? -pivmin * p : -pivmin;
+    neg += ((__double_as_longlong(pn) ^ __double_as_longlong(p)) < 0);   // sign change
+    pm1 = p;
+    p = pn;
 }
 
-// #{sigma < x} for x > 0
+__device__ __forceinline__ void sturm_rescale(double& pm1, double& p)
+{
+    const double m = fmax(fabs(pm1), fabs(p));
+    const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1023;   // -1023 for 0 / subnormal
+    if (ex > 400 || ex < -400) {
+        const double s = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, finite
+        pm1 *= s;
+        p *= s;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ int64_t count_below(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
                                                double x, double pivmin, double sc)
 {
-    double q = -x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    int64_t neg = 1;   // q_0 < 0
+    double pm1 = 1.0, p = -x;    // p_0, p_1
+    if (fabs(p) < pivmin) p = -pivmin;
+    int64_t neg = 1;             // p_0 > 0 > p_1
     for (int64_t k = 0; k < n; ++k) {
         // f_{2k} = d_k, then f_{2k+1} = e_k (absent after d_{n-1})
         const double dk = (double)__ldg(d + k) * sc;
-        q = fma(-dk * dk, rcp_newton(q), -x);
-        if (fabs(q) < pivmin) q = -pivmin;
-        neg += (q < 0.0);
+        sturm_step(pm1, p, dk * dk, x, pivmin, neg);
         if (k + 1 < n) {
             const double ek = (double)__ldg(e + k) * sc;
-            q = fma(-ek * ek, rcp_newton(q), -x);
-            if (fabs(q) < pivmin) q = -pivmin;
-            neg += (q < 0.0);
+            sturm_step(pm1, p, ek * ek, x, pivmin, neg);
         }
+        if (k & 1) sturm_rescale(pm1, p);
     }
     return neg - n;
 }
