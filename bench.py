@@ -9,6 +9,7 @@ Between timed steps the L2 is flushed by writing a 256 MiB buffer, so every
 step starts from HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --profile-case --n 8192 --b 128 --dtype f64 [--tw 32 --group 8 --reps 2]
 
 N > 1 runs one independent replica per GPU (the reduction of one matrix does
 not shard); the JSON value is the aggregate over ranks.  --impl reference times
@@ -132,12 +133,20 @@ def run_reference(args, rank, world):
             ms.append(dt * 1e3)
             gf.append(flops / dt / 1e9)
     value = float(np.median(gf))
+    # one step of our arm is the whole reduction: the sample's time scaled to
+    # the full schedule's flop count (the reduction's work model, host only)
+    from paper_2510_12705_gb300 import build as bbuild
+    bbuild.build()
+    import paper_2510_12705_gb300 as bb
+    full_flops = bb.bb_schedule_counts(n, b, tw).flops
+    ms_full = full_flops / (value * 1e9) * 1e3
     sample = (f"first {REF_STEP_SAMPLE} row-bulges (stage 1, sweeps 0..~{REF_STEP_SAMPLE // (n // b)}) "
               f"of the n={n}, b={b}, TW={tw} FP64 reduction, single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": ms_full, "ms_per_step_basis": "extrapolated: full-reduction flops / sampled rate",
+        "sample_ms": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"band->bidiag n={n} b={b} FP64 TW={tw}, N(0,1) seed {SEED}",
                    "n": n, "b": b, "tw": tw, "sample": sample},
@@ -149,12 +158,60 @@ def run_reference(args, rank, world):
     return 0
 
 
-# DRAM bytes (read + write) per launch of the bulge kernel, from one ncu capture
-# of this workload (profiles/bulge_kernel_dram_n32768_b128.md), keyed by the
-# launch configuration; None (reported as null) for any other configuration.
-MEASURED_DRAM_BYTES_PER_LAUNCH = {
-    ("bulge_kernel<double,33>", 32768, 128, 32, 0, 0): 440363008.0,
-}
+# DRAM bytes (read + write) per launch of a bulge-chasing kernel, from one ncu
+# capture of this workload, keyed by a hash of the kernel sources the capture
+# was taken with and by (kernel, n, b, tw); a changed kernel source or another
+# configuration reports null.
+MEASURED_DRAM_BYTES_PER_LAUNCH: dict = {}
+
+
+def kernel_source_hash() -> str:
+    """Short hash of the CUDA sources (csrc/*.cu, *.cuh) of the library."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2510_12705_gb300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_NAMES = {0: "group_kernel", 1: "team_kernel", 2: "bulge_kernel"}
+
+
+class LaunchTimer:
+    """CUDA events the library records around every bulge-chasing launch
+    (bb_tuning.ev_launch), with the (stage, kernel) of each launch."""
+
+    def __init__(self, torch, max_launches: int):
+        import ctypes
+        self.ctypes = ctypes
+        self.evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * max_launches)]
+        self.arr = (ctypes.c_void_p * len(self.evs))()
+        self.log = (ctypes.c_int * max_launches)()
+
+    def arm(self, tun, stream):
+        for i, ev in enumerate(self.evs):
+            ev.record(stream)                 # materialise the raw handles
+            self.arr[i] = ev.cuda_event
+        for i in range(len(self.log)):
+            self.log[i] = -1
+        tun.ev_launch = self.ctypes.cast(self.arr, self.ctypes.c_void_p)
+        tun.ev_count = len(self.evs)
+        tun.launch_log = self.ctypes.cast(self.log, self.ctypes.c_void_p)
+
+    def disarm(self, tun):
+        tun.ev_launch, tun.ev_count, tun.launch_log = None, 0, None
+
+    def read(self):
+        """[(stage, kernel id, ms)] of the launches of the last armed call."""
+        out = []
+        for i in range(len(self.log)):
+            if self.log[i] < 0:
+                break
+            out.append((self.log[i] // 4, self.log[i] % 4, self.evs[2 * i].elapsed_time(self.evs[2 * i + 1])))
+        return out
 
 
 def maxm_for(tw: int) -> int:
@@ -202,8 +259,11 @@ def run_ours(args, rank, world):
 
     def timed(band, d, e, tun, steps, warmup, work, bracket=False):
         """warmup untimed steps, then `steps` timed ones; every step starts
-        after an L2 flush; per-step CUDA events around the call and around
-        the bulge-chasing kernels (library-recorded)."""
+        after an L2 flush; per-step CUDA events around the call, around the
+        bulge-chasing kernels and around each of their launches (all recorded
+        by the library on `stream`)."""
+        lt = LaunchTimer(torch, 3 * max(work.stages, 1) + 2)
+        launches = []
         ws = torch.empty(bb.band_to_bidiag_workspace_size(n, b, bb._dtype_code(band.dtype), tun),
                          dtype=torch.uint8, device="cuda")
         for i in range(warmup):
@@ -227,10 +287,14 @@ def run_ours(args, rank, world):
                 ev.record(stream)
             tun.ev_start = k0.cuda_event
             tun.ev_stop = k1.cuda_event
+            lt.arm(tun, stream)
             e0.record(stream)
             bb.band_to_bidiag_ex(band, b, d, e, tuning=tun, workspace=ws, stream=stream)
             e1.record(stream)
             evs.append((e0, e1, k0, k1))
+            e1.synchronize()                   # read this step's launch events
+            launches.append(lt.read())
+        lt.disarm(tun)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         clk = None
@@ -242,7 +306,7 @@ def run_ours(args, rank, world):
         tun.ev_stop = None
         step_ms = [a.elapsed_time(z) for a, z, _, _ in evs]
         kern_ms = [a.elapsed_time(z) for _, _, a, z in evs]
-        return step_ms, kern_ms, wall, clk
+        return step_ms, kern_ms, wall, clk, launches
 
     # roofline denominators measured on this GPU
     peaks = _peaks_file() or {}
@@ -252,8 +316,8 @@ def run_ours(args, rank, world):
 
     # ---- timed region: K FP64 reductions (the headline), warm-up outside it
     clocks = ClockSampler(dev)
-    step_ms, kern_ms, wall, clk = timed(band64, d64, e64, t64, args.steps, args.warmup, work64,
-                                        bracket=True)
+    step_ms, kern_ms, wall, clk, launches64 = timed(band64, d64, e64, t64, args.steps, args.warmup,
+                                                    work64, bracket=True)
     status = bb.bb_device_status(stream, reset=True)
 
     ms_step = float(np.mean(step_ms))
@@ -265,7 +329,7 @@ def run_ours(args, rank, world):
     gflops = world * work64.flops / (ms_step * 1e-3) / 1e9
 
     # ---- FP32 form (same workload)
-    step32, kern32, _, _ = timed(band32, d32, e32, t32, args.steps, args.warmup, work32)
+    step32, kern32, _, _, launches32 = timed(band32, d32, e32, t32, args.steps, args.warmup, work32)
     ms32 = float(np.mean(step32))
     ms32_kern = float(np.mean(kern32))
 
@@ -297,21 +361,59 @@ def run_ours(args, rank, world):
 
     bytes64 = work64.bytes(8)
     bytes32 = work32.bytes(4)
-    achieved_fp64 = work64.flops / (ms_kern * 1e-3) / 1e9          # GFLOP/s
-    achieved_l2_64 = bytes64 / (ms_kern * 1e-3) / 1e9              # GB/s
+    stage64 = [bb.bb_stage_counts(n, b, t64.tw, i) for i in range(work64.stages)]
+    stage32 = [bb.bb_stage_counts(n, b, t32.tw, i) for i in range(work32.stages)]
+
+    def per_kernel(launches, stages, esize):
+        """Per kernel: launches per step, mean ms per step, and the work of
+        the stages it ran (one problem: one kernel per stage)."""
+        out = {}
+        steps = max(len(launches), 1)
+        for step in launches:
+            for st, kid, ms in step:
+                k = out.setdefault(KERNEL_NAMES.get(kid, str(kid)),
+                                   {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0, "stages": set()})
+                k["launches"] += 1
+                k["ms"] += ms
+                k["flops"] += stages[st].flops
+                k["bytes"] += stages[st].bytes(esize)
+                k["stages"].add(st)
+        for k in out.values():
+            k["launches_per_step"] = k.pop("launches") / steps
+            for f in ("ms", "flops", "bytes"):
+                k[f] /= steps
+            k["stages"] = sorted(k["stages"])
+        return out
+
+    kern64 = per_kernel(launches64, stage64, 8)
+    kern32 = per_kernel(launches32, stage32, 4)
+    dom = max(kern64, key=lambda k: kern64[k]["ms"]) if kern64 else "bulge_kernel"
+    dk = kern64.get(dom, {"ms": ms_kern, "flops": work64.flops, "bytes": bytes64, "launches_per_step": 1})
+    dom_name = f"{dom}<double,double,{maxm_for(t64.tw)}>"
+    achieved_fp64 = dk["flops"] / (dk["ms"] * 1e-3) / 1e9                  # GFLOP/s
+    achieved_l2_64 = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9                 # GB/s
     achieved_l2_32 = bytes32 / (ms32_kern * 1e-3) / 1e9
+    src_hash = kernel_source_hash()
+    traffic = MEASURED_DRAM_BYTES_PER_LAUNCH.get(src_hash, {}).get((dom_name, n, b, t64.tw))
     roofline = {
-        "bound": "alu", "kernel": f"bulge_kernel<double,{maxm_for(t64.tw)}>",
+        "bound": "alu", "kernel": dom_name,
         "achieved": achieved_fp64 / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
         "frac": achieved_fp64 / fp64_peak if fp64_peak > 0 else None,
+        "traffic": traffic,
         "peak_source": "measured FP64 FMA rate on this GPU (bb_measure_fma_peak)",
-        "traffic": MEASURED_DRAM_BYTES_PER_LAUNCH.get(
-            (f"bulge_kernel<double,{maxm_for(t64.tw)}>", n, b, t64.tw, t64.tpb, t64.sweeps_in_flight)),
+        "achieved_basis": "algorithmic flops of the stages this kernel ran / its launch time, "
+                          "CUDA events around each launch",
+        "kernel_share": dk["ms"] / ms_kern if ms_kern > 0 else None,
         "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-        "algorithmic_bytes_per_launch": bytes64 / max(work64.stages, 1),
+        "traffic_source": f"stored ncu capture for kernel sources {src_hash}" if traffic else
+                          "no ncu capture of the current kernel sources",
+        "algorithmic_bytes_per_launch": dk["bytes"] / max(dk["launches_per_step"], 1e-9),
         "l2": {"achieved": achieved_l2_64, "peak": l2_gbs, "unit": "GB/s",
                "frac": achieved_l2_64 / l2_gbs if l2_gbs > 0 else None,
                "peak_source": "measured L2-resident copy bandwidth (bb_measure_l2_bandwidth)"},
+        "whole_reduction": {"tflops": work64.flops / (ms_kern * 1e-3) / 1e12,
+                            "frac": (work64.flops / (ms_kern * 1e-3) / 1e9) / fp64_peak if fp64_peak > 0 else None},
+        "kernels": {k: {f: v[f] for f in ("ms", "launches_per_step", "stages", "flops")} for k, v in kern64.items()},
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
     fp32 = {
@@ -319,6 +421,7 @@ def run_ours(args, rank, world):
         "gflops": work32.flops / (ms32 * 1e-3) / 1e9,
         "speedup_vs_fp64": ms_step / ms32,
         "tw": t32.tw, "tpb": t32.tpb, "sweeps_in_flight": t32.sweeps_in_flight, "tuning": src32,
+        "kernels": {k: {f: v[f] for f in ("ms", "launches_per_step", "stages")} for k, v in kern32.items()},
         "roofline": {"bound": "l2", "achieved": achieved_l2_32, "peak": l2_gbs, "unit": "GB/s",
                      "frac": achieved_l2_32 / l2_gbs if l2_gbs > 0 else None,
                      "alu_frac": (work32.flops / (ms32_kern * 1e-3) / 1e9) / fp32_peak
@@ -341,7 +444,8 @@ def run_ours(args, rank, world):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"band->bidiag n={n} b={b} FP64 TW={t64.tw}, iid N(0,1) band, seed {SEED}",
                        "n": n, "b": b, "tw": t64.tw, "tpb": t64.tpb,
-                       "sweeps_in_flight": t64.sweeps_in_flight, "tuning": src64,
+                       "sweeps_in_flight": t64.sweeps_in_flight, "group": t64.group, "teams": t64.teams,
+                       "tuning": src64,
                        "stages": work64.stages, "row_bulges": work64.steps,
                        "flops_per_step": work64.flops, "algorithmic_bytes_per_step": bytes64,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas"},
@@ -351,8 +455,8 @@ def run_ours(args, rank, world):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
-            # pack + one persistent launch per stage + extract, per timed step
-            "gpu_launches": (2 + work64.stages) * args.steps,
+            # pack + the bulge-chasing launches + extract, per timed step
+            "gpu_launches": int(round((2 + sum(v["launches_per_step"] for v in kern64.values())) * args.steps)),
             "wall_s_timed_region": wall,
             "checks": {"device_status": status, "d0_exact": ok},
             "peaks_measured": {"fp64_gflops": fp64_peak, "fp32_gflops": fp32_peak, "l2_gbs": l2_gbs},
@@ -361,6 +465,67 @@ def run_ours(args, rank, world):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def profile_case(args):
+    """One configuration, reduced `reps` times (no L2 flush, no clocks): the
+    command the ncu summaries are taken with.  Prints one JSON line with the
+    kernel time of each repetition and its launches."""
+    import torch
+    import bandgen
+    import paper_2510_12705_gb300 as bb
+    from paper_2510_12705_gb300 import build as bbuild
+    bbuild.build()
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    code = bb.BB_F64 if args.dtype == "f64" else bb.BB_F32
+    n, b = args.n, args.b
+    band = torch.from_numpy(bandgen.random_band(n, b, seed=args.seed)).to("cuda", dt)
+    d = torch.empty(n, device="cuda", dtype=dt)
+    e = torch.empty(max(n - 1, 1), device="cuda", dtype=dt)
+    if args.tuned:
+        from paper_2510_12705_gb300 import tuner
+        tun, _ = tuner.tuning_for(n, b, args.dtype)
+    else:
+        tun = bb.bb_default_tuning(n, b, code)
+    for f in ("tw", "tpb", "group", "teams"):
+        if getattr(args, f):
+            setattr(tun, f, getattr(args, f))
+    if args.sif:
+        tun.sweeps_in_flight = args.sif
+    ws = torch.empty(bb.band_to_bidiag_workspace_size(n, b, code, tun), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    work = bb.bb_schedule_counts(n, b, tun.tw)
+    lt = LaunchTimer(torch, 3 * max(work.stages, 1) + 2)
+    runs = []
+    for _ in range(args.reps):
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for ev in (k0, k1):
+            ev.record(stream)
+        tun.ev_start, tun.ev_stop = k0.cuda_event, k1.cuda_event
+        lt.arm(tun, stream)
+        bb.band_to_bidiag_ex(band, b, d, e, tuning=tun, workspace=ws, stream=stream)
+        torch.cuda.synchronize()
+        runs.append({"kernel_ms": k0.elapsed_time(k1),
+                     "launches": [[st, KERNEL_NAMES.get(k, str(k)), round(ms, 3)] for st, k, ms in lt.read()]})
+    sig = None
+    if args.sigma:
+        s_out = torch.empty(n, device="cuda", dtype=torch.float64)
+        sws = torch.empty(int(bb.lib().bb_bidiag_sigma_workspace_size(n)), dtype=torch.uint8,
+                          device="cuda")
+        bb.bb_bidiag_sigma(d, e, s_out, sws, stream=stream)          # warm-up
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        bb.bb_bidiag_sigma(d, e, s_out, sws, stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sig = {"sigma_ms": s0.elapsed_time(s1), "sigma_max": float(s_out[0]),
+               "sigma_min": float(s_out[-1])}
+    status = bb.bb_device_status(stream, reset=True)
+    print(json.dumps({"n": n, "b": b, "dtype": args.dtype, "tw": tun.tw, "group": tun.group,
+                      "teams": tun.teams, "tpb": tun.tpb, "sweeps_in_flight": tun.sweeps_in_flight,
+                      "status": status, "flops": work.flops, "row_bulges": work.steps, "runs": runs,
+                      "sigma": sig}))
+    return 0 if status == 0 else 1
 
 
 def main():
@@ -372,7 +537,21 @@ def main():
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--b", type=int, default=B)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="reduce one configuration --reps times and print its kernel times")
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--tw", type=int, default=0)
+    ap.add_argument("--tpb", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--teams", type=int, default=0)
+    ap.add_argument("--sif", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=SEED)
+    ap.add_argument("--tuned", action="store_true", help="profile case: the trained tuner's choice")
+    ap.add_argument("--sigma", action="store_true", help="profile case: also time the GPU sigma")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

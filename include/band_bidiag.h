@@ -77,7 +77,23 @@ extern "C" {
  *                    (default 5 s)
  *   ev_start/ev_stop optional cudaEvent_t handles (NULL = none): recorded on the
  *                    call's stream immediately before and after the persistent
- *                    bulge-chasing kernel, so a caller can time that kernel alone
+ *                    bulge-chasing kernels, so a caller can time them alone
+ *   group            sweeps one CTA chases together through shared memory (the
+ *                    paper's "max blocks" unrolled into one block): 0 = default,
+ *                    -1 = one sweep per CTA on every stage, k >= 1 = at most k.
+ *                    A stage (bw -> bw - d) takes min(k, (bw - d) / 3) sweeps per
+ *                    CTA; other stages but the last run one sweep per CTA.
+ *   teams            sweeps one CTA runs side by side on the last stage (the one
+ *                    that ends at bandwidth 1), one warp each, on a shared-memory
+ *                    window: 0 = default (one sweep per CTA), -1 = one sweep per
+ *                    CTA, k >= 1 = at most k (fewer when the window would not
+ *                    fit shared memory)
+ *   ev_launch/ev_count/launch_log  optional per-launch timing (NULL / 0 = none):
+ *                    ev_launch is an array of ev_count cudaEvent_t handles;
+ *                    launch i of the bulge-chasing kernels is bracketed by
+ *                    events 2i and 2i+1 (while 2i+1 < ev_count), and, when
+ *                    launch_log (host, ev_count / 2 ints) is given, its entry i
+ *                    is set to 4 * stage + kernel (0 group, 1 team, 2 per-sweep)
  */
 typedef struct {
     int tw;
@@ -87,6 +103,11 @@ typedef struct {
     double timeout_s;
     void *ev_start;
     void *ev_stop;
+    int group;
+    int teams;
+    void **ev_launch;
+    int ev_count;
+    int *launch_log;
 } bb_tuning;
 
 /* one problem of a batch: fields as in band_to_bidiag() */
@@ -159,11 +180,27 @@ int bb_batch_execute(const bb_batch_plan *plan, void *workspace, size_t workspac
 void bb_batch_plan_destroy(bb_batch_plan *plan);
 
 /*
+ * band_to_bidiag_batched -- the plan API in one call: plans the `count`
+ * problems (host array of descriptors holding device pointers, one dtype),
+ * takes the workspace from the stream-ordered allocator on `stream`, enqueues
+ * the reduction (pack, one persistent launch per stage and kernel, extract)
+ * and releases the workspace on `stream`.  The problem table is copied to the
+ * device from pageable host memory, so the caller's array may be reused as
+ * soon as the call returns.  Asynchronous; device-side errors go to the
+ * status word.  Returns BB_OK, BB_ERR_ARG, BB_ERR_ALLOC, BB_ERR_UNSUPPORTED or
+ * BB_ERR_LAUNCH.
+ */
+int band_to_bidiag_batched(int count, const bb_problem *problems, int dtype, void *stream);
+
+/*
  * Device status: synchronises `stream`, returns the sticky status word of the
  * current device (bit (1 << code) set for each device-side error code seen
  * since the last reset) and clears it when `reset` is non-zero.
  */
 int bb_device_status(void *stream, int reset);
+
+/* bb_device_status(stream, 1): read and clear (blocks until `stream` is idle) */
+int bb_last_device_status(void *stream);
 
 /* human-readable name of a status code */
 const char *bb_status_string(int code);
@@ -177,6 +214,10 @@ const char *bb_status_string(int code);
  */
 int bb_schedule_counts(int64_t n, int64_t b, int tw, int64_t *stages, int64_t *steps,
                        double *flops, double *elements);
+
+/* the same for stage `stage` only (0-based; *stages = total number of stages) */
+int bb_stage_counts(int64_t n, int64_t b, int tw, int stage, int64_t *stages, int64_t *steps,
+                    double *flops, double *elements);
 
 /* built-in default tuning for (n, b, dtype) */
 int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning *out);

@@ -19,6 +19,7 @@ Parity status of each function:
                       Jacobi / LAPACK SVD brute force, prescribed-sigma inputs.
   bidiag_sigma        pinned: against numpy SVD of the dense bidiagonal and
                       against closed-form bidiagonal spectra.
+  bidiag_count_below  pinned: against exact rational Sturm counts.
   jacobi_sigma        pinned: against numpy SVD and diagonal matrices.
   band_power_sums     pinned: against dense numpy on small matrices.
 """
@@ -75,6 +76,8 @@ def _load():
             lib.oracle_band_to_bidiag.restype = ctypes.c_int
             lib.oracle_bidiag_sigma.argtypes = [ctypes.c_int, dp, dp, dp]
             lib.oracle_bidiag_sigma.restype = ctypes.c_int
+            lib.oracle_gk_count.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double]
+            lib.oracle_gk_count.restype = ctypes.c_longlong
             lib.oracle_jacobi_sigma.argtypes = [ctypes.c_int, dp, dp]
             lib.oracle_jacobi_sigma.restype = ctypes.c_int
             _lib = lib
@@ -155,6 +158,15 @@ def bidiag_sigma(d: np.ndarray, e: np.ndarray, method: str = "auto") -> np.ndarr
         w = eigvalsh_tridiagonal(np.zeros(2 * n), off, lapack_driver="sterf")
         return np.sort(np.abs(w[n:]))[::-1]
     raise ValueError(method)
+
+
+def bidiag_count_below(d: np.ndarray, e: np.ndarray, x: float, pivmin: float) -> int:
+    """#{sigma < x} (x > 0) of the bidiagonal (d, e): the oracle's Sturm count
+    in pivot form on the Golub-Kahan matrix (tiny pivots replaced by -pivmin)."""
+    lib = _load()
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(e if len(e) else np.zeros(1), dtype=np.float64)
+    return int(lib.oracle_gk_count(len(d), _ptr(d), _ptr(e), float(x), float(pivmin)))
 
 
 def jacobi_sigma(a: np.ndarray) -> np.ndarray:

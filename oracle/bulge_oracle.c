@@ -302,6 +302,13 @@ static long long gk_count_below(int n, const double *d, const double *e, double 
     return neg;
 }
 
+/* #{sigma < x} of the bidiagonal (d, e) for x > 0: the negative pivots of the
+ * Golub-Kahan matrix shifted by x, minus n (exported for the tests) */
+long long oracle_gk_count(int n, const double *d, const double *e, double x, double pivmin)
+{
+    return gk_count_below(n, d, e, x, pivmin) - n;
+}
+
 int oracle_bidiag_sigma(int n, const double *d, const double *e, double *sigma_out)
 {
     if (n < 1) return -1;

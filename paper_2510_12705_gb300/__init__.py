@@ -9,7 +9,8 @@ used for device memory and streams.  The functions keep the C names:
     band_to_bidiag_host(band_np, b, tuning=None) -> (d, e)
     band_to_bidiag_workspace_size(n, b, dtype, tuning=None)
     BatchPlan(problems, dtype, tuning)       # bb_batch_plan_*
-    bb_device_status(stream=None, reset=True)
+    band_to_bidiag_batched(problems, stream=None)
+    bb_device_status(stream=None, reset=True), bb_last_device_status(stream=None)
     bb_schedule_counts(n, b, tw), bb_default_tuning(n, b, dtype)
     bb_measure_l2_bandwidth(bytes, reps), bb_measure_fma_peak(dtype)
 
@@ -52,7 +53,9 @@ class BBError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("tw", ctypes.c_int), ("tpb", ctypes.c_int), ("sweeps_in_flight", ctypes.c_int),
                 ("flags", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("ev_start", ctypes.c_void_p), ("ev_stop", ctypes.c_void_p)]
+                ("ev_start", ctypes.c_void_p), ("ev_stop", ctypes.c_void_p), ("group", ctypes.c_int),
+                ("teams", ctypes.c_int), ("ev_launch", ctypes.c_void_p), ("ev_count", ctypes.c_int),
+                ("launch_log", ctypes.c_void_p)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,11 +87,15 @@ def lib():
             "bb_batch_execute": (ci, [vp, vp, sz, vp]),
             "bb_batch_plan_destroy": (None, [vp]),
             "bb_device_status": (ci, [vp, ci]),
+            "bb_last_device_status": (ci, [vp]),
+            "band_to_bidiag_batched": (ci, [ci, ctypes.POINTER(Problem), ci, vp]),
             "bb_status_string": (ctypes.c_char_p, [ci]),
             "bb_schedule_counts": (ci, [i64, i64, ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
             "bb_default_tuning": (ci, [i64, i64, ci, tp]),
+            "bb_stage_counts": (ci, [i64, i64, ci, ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "bb_measure_l2_bandwidth": (ctypes.c_double, [sz, ci, vp]),
             "bb_measure_fma_peak": (ctypes.c_double, [ci, vp]),
             "bb_autotune": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, ci, ci,
@@ -245,6 +252,15 @@ class ScheduleCounts:
         return 2.0 * self.elements * elem_size
 
 
+def bb_stage_counts(n: int, b: int, tw: int, stage: int) -> ScheduleCounts:
+    """Work model of one stage (``stages`` is the total number of stages)."""
+    st, sp = ctypes.c_int64(), ctypes.c_int64()
+    fl, el = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bb_stage_counts(n, b, tw, stage, ctypes.byref(st), ctypes.byref(sp),
+                                 ctypes.byref(fl), ctypes.byref(el)), "bb_stage_counts")
+    return ScheduleCounts(st.value, sp.value, fl.value, el.value)
+
+
 def bb_schedule_counts(n: int, b: int, tw: int) -> ScheduleCounts:
     st, sp = ctypes.c_int64(), ctypes.c_int64()
     fl, el = ctypes.c_double(), ctypes.c_double()
@@ -298,6 +314,26 @@ class BatchPlan:
         if p and _lib is not None:
             _lib.bb_batch_plan_destroy(p)
             self._plan = None
+
+
+def band_to_bidiag_batched(problems, stream=None) -> None:
+    """One call for a batch: ``problems`` is a list of (band, b, d_out, e_out)
+    CUDA tensors of one dtype; the workspace comes from the stream-ordered
+    allocator (see BatchPlan for a reusable, graph-capturable plan)."""
+    dt = problems[0][0].dtype
+    arr = (Problem * len(problems))()
+    for i, (band, b, d, e) in enumerate(problems):
+        n, ldab = _check_band(band, d, e)
+        if band.dtype != dt:
+            raise ValueError("all problems of a batch share one dtype")
+        arr[i] = Problem(n, b, band.data_ptr(), ldab, d.data_ptr(), e.data_ptr() if n > 1 else None)
+    _check(lib().band_to_bidiag_batched(len(problems), arr, _dtype_code(dt), _stream_handle(stream)),
+           "band_to_bidiag_batched")
+
+
+def bb_last_device_status(stream=None) -> int:
+    """bb_device_status(stream, reset=True)."""
+    return int(lib().bb_last_device_status(_stream_handle(stream)))
 
 
 def band_to_bidiag_noalloc(band, b: int, d_out, e_out, stream=None) -> None:

@@ -28,6 +28,8 @@
 
 #include "../../include/band_bidiag.h"
 #include "bb_device.cuh"
+#include "bb_group.cuh"
+#include "bb_team.cuh"
 
 using namespace bb;
 
@@ -395,6 +397,8 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         const int n = D.n;
         const int bw = stage_bw(D.b, L.tw, stage);
         const int d = stage_d(bw, L.tw);
+        if (L.gK > 0 && group_members(bw, d, L.gK) >= 1) continue;   // the group kernel's
+        if (L.team > 0 && bw - d == 1) continue;                      // the team kernel's
         const bool split = (bw - d) >= 2;
         const int base = stage * PROG_STAGE;
         int* prog = L.prog + D.prog_off;
@@ -501,10 +505,20 @@ int maxm_for(int tw)
     return 33;
 }
 
+// sweeps per CTA of the group kernel when the tuning leaves it open
+constexpr int kDefaultGroup = 8;
+// sweeps per CTA of the team kernel (last stage) when the tuning leaves it
+// open: 0, the per-sweep kernel runs the last stage unless a tuning asks for
+// the team kernel (it is slower than the per-sweep kernel as it stands)
+constexpr int kDefaultTeams = 0;
+
 struct Resolved {
-    int dtype, tw, tpb, sif, flags;
+    int dtype, tw, tpb, sif, flags, group, teams;
     unsigned long long timeout_ns;
     cudaEvent_t ev_start, ev_stop;
+    void** ev_launch;
+    int ev_count;
+    int* launch_log;
 };
 
 bool resolve_tuning(int64_t n, int64_t b, int dtype, const bb_tuning* t, Resolved* r)
@@ -516,12 +530,20 @@ bool resolve_tuning(int64_t n, int64_t b, int dtype, const bb_tuning* t, Resolve
     r->tpb = (t && t->tpb > 0) ? t->tpb : def.tpb;
     r->sif = (t && t->sweeps_in_flight > 0) ? t->sweeps_in_flight : 0;
     r->flags = t ? t->flags : 0;
+    r->group = (t && t->group != 0) ? (t->group < 0 ? 0 : t->group) : kDefaultGroup;
+    r->teams = (t && t->teams != 0) ? (t->teams < 0 ? 0 : t->teams) : kDefaultTeams;
     const double to = (t && t->timeout_s > 0) ? t->timeout_s : def.timeout_s;
     r->timeout_ns = (unsigned long long)(to * 1e9);
     r->ev_start = t ? (cudaEvent_t)t->ev_start : nullptr;
     r->ev_stop = t ? (cudaEvent_t)t->ev_stop : nullptr;
+    r->ev_launch = t ? t->ev_launch : nullptr;
+    r->ev_count = t ? t->ev_count : 0;
+    r->launch_log = t ? t->launch_log : nullptr;
     if (r->tw < 1 || r->tw > 32) return false;
     if (r->tpb != 0 && (r->tpb < 64 || r->tpb > 512 || r->tpb % 32 != 0)) return false;
+    if (t && (t->group < -1 || t->teams < -1)) return false;
+    if (r->group > 64) r->group = 64;
+    if (r->teams > 16) r->teams = 16;
     return true;
 }
 
@@ -533,8 +555,45 @@ struct LaunchPlan {
     int max_b = 0;
     size_t off_hdr = 0, off_stage = 0, off_prog = 0, off_desc = 0, off_w = 0, bytes = 0;
     size_t smem = 0;
+    size_t gsmem = 0;     // dynamic shared memory of the group kernel (0: not used)
+    size_t tsmem = 0;     // dynamic shared memory of the team kernel (0: not used)
     Resolved tune;
 };
+
+// Dynamic shared memory of the group kernel with at most K sweeps per CTA:
+// the largest window over the stages and problems it takes (0 when it takes
+// none).
+size_t group_smem_bytes(const LaunchPlan& P, int K)
+{
+    if (K < 1) return 0;
+    const int tw = P.tune.tw, maxm = maxm_for(tw);
+    const size_t es = P.tune.dtype == BB_F64 ? 8 : 4;
+    int window = 0;
+    for (const Desc& D : P.descs)
+        for (int st = 0; st < D.nstages; ++st) {
+            const int bw = D.b - st * tw, d = std::min(tw, bw - 1);
+            const int k = group_members(bw, d, K);
+            if (k >= 1) window = std::max(window, group_window_elems(bw, d, k));
+        }
+    if (window == 0) return 0;
+    return es * (size_t)(group_small_elems(K, maxm) + window);
+}
+
+// Dynamic shared memory of the team kernel with W sweeps per CTA: the largest
+// last-stage window over the problems (0 when no problem has a last stage).
+size_t team_smem_bytes(const LaunchPlan& P, int W)
+{
+    if (W < 1) return 0;
+    const int tw = P.tune.tw, maxm = maxm_for(tw);
+    const size_t es = P.tune.dtype == BB_F64 ? 8 : 4;
+    int elems = 0;
+    for (const Desc& D : P.descs) {
+        if (D.nstages < 1) continue;
+        const int bw = D.b - (D.nstages - 1) * tw;     // the last stage ends at bandwidth 1
+        elems = std::max(elems, team_smem_elems(bw, W, maxm));
+    }
+    return es * (size_t)elems;
+}
 
 // Lay out a launch for `count` problems (host-side planning, no CUDA calls).
 int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* tuning,
@@ -616,6 +675,10 @@ int plan_launch(int count, const bb_problem* probs, int dtype, const bb_tuning* 
     // panels hold the compute type: FP64 for the FP64 form, FP32 otherwise
     P->smem = (size_t)(dtype == BB_F64 ? 8 : 4) * ((size_t)maxm_for(tw) + 1) * (size_t)(L.rp_rows + L.lp_cols);
     if (L.total_tasks >= (int64_t)INT32_MAX) return BB_ERR_UNSUPPORTED;
+    L.gK = P->tune.group;
+    P->gsmem = group_smem_bytes(*P, L.gK);
+    L.team = P->tune.teams;
+    P->tsmem = team_smem_bytes(*P, L.team);
     return BB_OK;
 }
 
@@ -638,47 +701,113 @@ int stage_tpb(int bw, int d, int user_tpb)
     return std::max(96, std::min(512, t));
 }
 
+// threads of the group kernel for a stage: 16 panel rows / columns per warp
+// and pass, one pass over the left reflector's columns
+// (at most 384: the kernel is compiled for two CTAs of 384 threads per SM)
+int group_tpb(int bw, int d, int user_tpb)
+{
+    if (user_tpb > 0) return std::min(user_tpb, 384);
+    const int warps = (bw + d + 1 + 15) / 16;
+    return std::max(128, std::min(384, 32 * warps));
+}
+
+template <typename K>
+int set_smem(K kern, size_t bytes)
+{
+    if (bytes > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+        cudaGetLastError();   // not sticky: leave no error for the caller's next launch
+        return BB_ERR_UNSUPPORTED;
+    }
+    return BB_OK;
+}
+
+// One launch per stage and kernel: the group kernel for the problems whose
+// stage takes at least one sweep per group (3K + d <= bw), the team kernel for
+// the problems on their last stage (it ends at bandwidth 1), the per-sweep
+// kernel for the rest.  The three persistent kernels claim tasks in order from
+// the header's counter, which is reset before every launch.
 template <typename TS, typename T, int MAXM>
 int launch_stages(const LaunchPlan& P, cudaStream_t st)
 {
     auto kern = bulge_kernel<TS, T, MAXM>;
-    if (P.smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) != cudaSuccess) {
-            cudaGetLastError();   // not sticky: leave no error for the caller's next launch
-            return BB_ERR_UNSUPPORTED;
-        }
-    }
+    auto gkern = group_kernel<TS, T, MAXM>;
+    auto tkern = team_kernel<TS, T, MAXM>;
+    int rc = set_smem(kern, P.smem);
+    if (rc == BB_OK && P.gsmem) rc = set_smem(gkern, P.gsmem);
+    if (rc == BB_OK && P.tsmem) rc = set_smem(tkern, P.tsmem);
+    if (rc != BB_OK) return rc;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (P.tune.ev_start && cudaEventRecord(P.tune.ev_start, st) != cudaSuccess) return BB_ERR_LAUNCH;
     Launch L = P.L;
+    if (!P.gsmem) L.gK = 0;
+    if (!P.tsmem) L.team = 0;
+    bool first = true;
+    int nlaunch = 0;
     for (int stage = 0; stage < P.max_stages; ++stage) {
-        // widest stage-i bandwidth over the problems sizes the CTA
-        int bw_max = 0, d_max = 0;
+        // widest stage bandwidth over the problems of each kernel, and the
+        // tasks (problems x groups) of the group and team kernels
+        int bw_max = 0, d_max = 0, gbw_max = 0, gd_max = 0;
+        int64_t gtasks = 0, ttasks = 0;
+        bool any_sweep = false;
         for (const Desc& D : P.descs)
             if (stage < D.nstages) {
-                const int bw = D.b - stage * L.tw;
-                bw_max = std::max(bw_max, bw);
-                d_max = std::max(d_max, std::min(L.tw, bw - 1));
+                const int bw = D.b - stage * L.tw, d = std::min(L.tw, bw - 1);
+                const int k = L.gK ? group_members(bw, d, L.gK) : 0;
+                if (k >= 1) {
+                    gbw_max = std::max(gbw_max, bw);
+                    gd_max = std::max(gd_max, d);
+                    const int nact = D.n - 1 - (bw - d);
+                    gtasks = std::max<int64_t>(gtasks, nact > 0 ? (nact + k - 1) / k : 0);
+                } else if (L.team && bw - d == 1) {
+                    const int nact = D.n - 2;
+                    ttasks = std::max<int64_t>(ttasks, nact > 0 ? (nact + L.team - 1) / L.team : 0);
+                } else {
+                    any_sweep = true;
+                    bw_max = std::max(bw_max, bw);
+                    d_max = std::max(d_max, d);
+                }
             }
-        const int tpb = stage_tpb(bw_max, d_max, P.tune.tpb);
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, P.smem) != cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            return BB_ERR_UNSUPPORTED;
-        }
-        int64_t grid = (int64_t)nsm * per_sm;
-        if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
-        grid = std::min<int64_t>(grid, L.total_tasks);
-        if (grid < 1) continue;
         L.stage = stage;
-        // each stage restarts the claim counter (a tiny kernel-free reset)
-        if (stage > 0 && cudaMemsetAsync(&P.L.hdr->claim, 0, sizeof(int), st) != cudaSuccess)
-            return BB_ERR_LAUNCH;
-        kern<<<(unsigned)grid, tpb, P.smem, st>>>(L);
-        if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
+        for (int which = 0; which < 3; ++which) {
+            if (which == 0 ? gtasks == 0 : which == 1 ? ttasks == 0 : !any_sweep) continue;
+            const int tpb = which == 0 ? group_tpb(gbw_max, gd_max, P.tune.tpb)
+                          : which == 1 ? 32 * (L.team + 1)
+                                       : stage_tpb(bw_max, d_max, P.tune.tpb);
+            const size_t smem = which == 0 ? P.gsmem : which == 1 ? P.tsmem : P.smem;
+            int per_sm = 0;
+            const cudaError_t oe =
+                which == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gkern, tpb, smem)
+              : which == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tkern, tpb, smem)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
+            if (oe != cudaSuccess || per_sm < 1) {
+                cudaGetLastError();
+                return BB_ERR_UNSUPPORTED;
+            }
+            Launch LL = L;
+            LL.total_tasks = which == 0 ? (int64_t)L.count * gtasks
+                           : which == 1 ? (int64_t)L.count * ttasks : L.total_tasks;
+            int64_t grid = (int64_t)nsm * per_sm;
+            if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
+            grid = std::min<int64_t>(grid, LL.total_tasks);
+            if (grid < 1) continue;
+            if (!first && cudaMemsetAsync(&P.L.hdr->claim, 0, sizeof(int), st) != cudaSuccess)
+                return BB_ERR_LAUNCH;
+            first = false;
+            cudaEvent_t* ev = (cudaEvent_t*)P.tune.ev_launch;
+            const bool rec = ev && 2 * nlaunch + 1 < P.tune.ev_count;
+            if (rec && cudaEventRecord(ev[2 * nlaunch], st) != cudaSuccess) return BB_ERR_LAUNCH;
+            if (which == 0) gkern<<<(unsigned)grid, tpb, smem, st>>>(LL);
+            else if (which == 1) tkern<<<(unsigned)grid, tpb, smem, st>>>(LL);
+            else kern<<<(unsigned)grid, tpb, smem, st>>>(LL);
+            if (cudaGetLastError() != cudaSuccess) return BB_ERR_LAUNCH;
+            if (rec && cudaEventRecord(ev[2 * nlaunch + 1], st) != cudaSuccess) return BB_ERR_LAUNCH;
+            if (P.tune.launch_log && nlaunch < P.tune.ev_count / 2)
+                P.tune.launch_log[nlaunch] = stage * 4 + which;
+            ++nlaunch;
+        }
     }
     if (P.tune.ev_stop && cudaEventRecord(P.tune.ev_stop, st) != cudaSuccess) return BB_ERR_LAUNCH;
     return BB_OK;
@@ -719,6 +848,11 @@ int enqueue(LaunchPlan* P, void* ws, const void* host_descs, cudaStream_t st)
         cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return BB_ERR_LAUNCH;
     if (P->max_stages > 0 && P->smem > (size_t)smem_optin) return BB_ERR_UNSUPPORTED;
+    // a group window larger than the device allows: fewer sweeps per CTA
+    while (P->gsmem > (size_t)smem_optin && P->L.gK > 1) P->gsmem = group_smem_bytes(*P, --P->L.gK);
+    if (P->gsmem > (size_t)smem_optin) { P->gsmem = 0; P->L.gK = 0; }
+    while (P->tsmem > (size_t)smem_optin && P->L.team > 1) P->tsmem = team_smem_bytes(*P, --P->L.team);
+    if (P->tsmem > (size_t)smem_optin) { P->tsmem = 0; P->L.team = 0; }
     bind_workspace(P, ws);
     if (cudaMemsetAsync(ws, 0, P->off_w, st) != cudaSuccess) return BB_ERR_LAUNCH;
     if (P->L.count > 1) {
@@ -751,6 +885,11 @@ int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning* out)
     out->timeout_s = 5.0;
     out->ev_start = nullptr;
     out->ev_stop = nullptr;
+    out->group = 0;                           // default sweeps per CTA (kDefaultGroup)
+    out->teams = 0;                           // default sweeps per CTA on the last stage
+    out->ev_launch = nullptr;
+    out->ev_count = 0;
+    out->launch_log = nullptr;
     return BB_OK;
 }
 
@@ -782,7 +921,7 @@ size_t bb_shared_bytes(int64_t n, int64_t b, int dtype, const bb_tuning* tuning)
     bb_problem p = {n, b, (const void*)16, b + 1, (void*)16, (void*)16};
     LaunchPlan P;
     if (plan_launch(1, &p, dtype, tuning, &P) != BB_OK) return 0;
-    return P.smem;
+    return std::max(P.smem, std::max(P.gsmem, P.tsmem));
 }
 
 int band_to_bidiag_ex(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab,
@@ -824,6 +963,8 @@ int bb_device_status(void* stream, int reset)
     }
     return (int)v;
 }
+
+int bb_last_device_status(void* stream) { return bb_device_status(stream, 1); }
 
 int band_to_bidiag_host(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab,
                         void* d_out, void* e_out, const bb_tuning* tuning, void* stream)
@@ -897,6 +1038,20 @@ int bb_batch_execute(const bb_batch_plan* plan, void* workspace, size_t workspac
     return enqueue(&P, workspace, plan->pinned, (cudaStream_t)stream);
 }
 
+int band_to_bidiag_batched(int count, const bb_problem* problems, int dtype, void* stream)
+{
+    LaunchPlan P;
+    int rc = plan_launch(count, problems, dtype, nullptr, &P);
+    if (rc != BB_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    void* ws = nullptr;
+    if (cudaMallocAsync(&ws, P.bytes, st) != cudaSuccess) return BB_ERR_ALLOC;
+    // the table goes from pageable memory, which the copy consumes before it returns
+    rc = enqueue(&P, ws, count > 1 ? (const void*)P.descs.data() : nullptr, st);
+    cudaFreeAsync(ws, st);
+    return rc;
+}
+
 void bb_batch_plan_destroy(bb_batch_plan* plan)
 {
     if (!plan) return;
@@ -908,6 +1063,12 @@ void bb_batch_plan_destroy(bb_batch_plan* plan)
 
 int bb_schedule_counts(int64_t n64, int64_t b64, int tw, int64_t* stages_out, int64_t* steps_out,
                        double* flops_out, double* elems_out)
+{
+    return bb_stage_counts(n64, b64, tw, -1, stages_out, steps_out, flops_out, elems_out);
+}
+
+int bb_stage_counts(int64_t n64, int64_t b64, int tw, int stage, int64_t* stages_out,
+                    int64_t* steps_out, double* flops_out, double* elems_out)
 {
     if (n64 < 1 || b64 < 0 || tw < 1 || n64 >= PROG_STAGE) return BB_ERR_ARG;
     const int n = (int)n64;
@@ -927,6 +1088,10 @@ int bb_schedule_counts(int64_t n64, int64_t b64, int tw, int64_t* stages_out, in
     for (int bw = b; bw > 1;) {
         const int d = std::min(tw, bw - 1);
         ++stages;
+        if (stage >= 0 && stages - 1 != stage) {   // only the requested stage
+            bw -= d;
+            continue;
+        }
         for (int R = 0; R < n - 1; ++R) {
             const int c0 = R + bw - d;
             if (c0 >= n - 1) continue;

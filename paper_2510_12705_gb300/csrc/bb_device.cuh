@@ -131,6 +131,11 @@ struct Launch {
     int rp_rows;          // shared-memory right panel rows (>= max b + TW + 1)
     int lp_cols;          // shared-memory left panel columns (>= max b + TW + 1)
     int stage;            // bandwidth-reduction stage of this launch
+    int gK;               // sweeps per CTA of the group kernel (0: every stage runs
+                          // one sweep per CTA); the per-sweep kernel skips the
+                          // problems the group kernel takes on this stage
+    int team;             // sweeps per CTA of the team kernel on the last stage
+                          // (0: the per-sweep kernel runs it)
 };
 
 __device__ __forceinline__ const Desc& desc_of(const Launch& L, int q)
@@ -310,17 +315,22 @@ __device__ __forceinline__ void warp_reflector(int m, const T* x, T* ts, T* v, T
 // waiting CTAs do not flood the L2 slice that holds the word).  Gives up (sets
 // the error and abort words and returns false) when the watched word has not
 // changed for timeout_ns, or when another CTA aborted.  Called by one thread.
+// The polls are relaxed loads; one acquire load follows once the target is
+// seen (the words only grow, so it reads a value >= target and synchronises
+// with the release that wrote it).  An acquire at GPU scope also discards the
+// SM's L1 contents, so polling with it would stall the other warps and CTAs
+// of the SM on every poll.
 __device__ bool wait_at_least(const int* addr, int target, Header* hdr,
                               unsigned long long timeout_ns)
 {
-    int last = ld_acquire(addr);
-    if (last >= target) return true;
+    int last = ld_relaxed(addr);
+    if (last >= target) { (void)ld_acquire(addr); return true; }
     unsigned long long t_last = global_ns();
     for (;;) {
         const int gap = target - last;
         __nanosleep(gap > 2 ? 2000u : (gap == 2 ? 400u : 64u));
-        const int v = ld_acquire(addr);
-        if (v >= target) return true;
+        const int v = ld_relaxed(addr);
+        if (v >= target) { (void)ld_acquire(addr); return true; }
         if (ld_relaxed(&hdr->abort)) return false;
         const unsigned long long now = global_ns();
         if (v != last) { last = v; t_last = now; continue; }
@@ -329,6 +339,147 @@ __device__ bool wait_at_least(const int* addr, int target, Header* hdr,
             atomicExch(&hdr->abort, 1);
             return false;
         }
+    }
+}
+
+}  // namespace bb
+
+namespace bb {
+
+// ---------------------------------------------- short-chain reflector (warp)
+// FP64 approximations from the hardware's special-function unit (PTX
+// rsqrt.approx / rcp.approx), refined below by published iterations.
+__device__ __forceinline__ double rsqrt_approx(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+__device__ __forceinline__ double rcp_approx(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
+// Warp-cooperative Householder vector with the xLARFG contract (as
+// warp_reflector), written for a short dependent chain: each dependent FP64
+// operation costs about 63 cycles on this GPU, so the chain, not the
+// arithmetic, sets the time of a reflector.
+//   sum of squares  FP32 data: exact in 64-bit fixed point (each square is a
+//                   48-bit integer; aligned to the largest exponent with 9
+//                   bits of headroom for 33 terms, the truncation of small
+//                   terms is below 2^-52 of the sum), one conversion to FP64;
+//                   FP64 data: scaled by the power of two that brings the
+//                   largest entry into [1, 4), squares summed in FP64.
+//   norm            Goldschmidt's coupled iteration for sqrt(s) and
+//                   1/(2 sqrt(s)) from the rsqrt.approx seed (STEPS steps).
+//   1 / (|alpha| + norm)  Newton-Raphson from the rcp.approx seed.
+// STEPS = 1 gives about 2^-44 (results rounded to FP32), 2 full FP64.
+// x[0..m) in shared memory (m <= 64) -> v[0..MAXM) (zero beyond m),
+// tb = {tau, beta, ...}; tau = 0 and v = e1 when x[1..m) is zero.
+template <typename T, int MAXM>
+__device__ __forceinline__ void fast_reflector(int m, const T* x, T* v, T* tb)
+{
+    const int lane = threadIdx.x & 31;
+    constexpr int STEPS = sizeof(T) == 8 ? 2 : 1;
+    const T x0 = lane < m ? x[lane] : (T)0;
+    const T x1 = lane + 32 < m ? x[lane + 32] : (T)0;
+    const T alpha = __shfl_sync(FULL, x0, 0);
+    const bool zero = (m <= 1) || !__any_sync(FULL, (lane >= 1 && x0 != (T)0) || x1 != (T)0);
+    if (zero) {
+        for (int t = lane; t < MAXM; t += 32) v[t] = (T)(t == 0 ? 1 : 0);
+        if (lane == 0) { tb[0] = (T)0; tb[1] = alpha; tb[2] = (T)0; }
+        return;
+    }
+    double s2, inv_sc = 1.0;   // sum of squares of the (scaled) vector; 1 / scale
+    double t0, t1;             // this lane's (scaled) entries in FP64
+    if constexpr (sizeof(T) == 4) {
+        // exact fixed-point sum of squares of FP32 values
+        auto split = [](float f, unsigned& e, unsigned long long& q) {
+            const unsigned u = __float_as_uint(f);
+            e = (u >> 23) & 0xffu;
+            unsigned mant = u & 0x7fffffu;
+            if (e) mant |= 0x800000u; else e = 1;   // subnormal: exponent field 1
+            q = (unsigned long long)mant * mant;     // < 2^48
+            if (mant == 0) e = 0;
+        };
+        unsigned e0, e1;
+        unsigned long long q0, q1;
+        split((float)x0, e0, q0);
+        split((float)x1, e1, q1);
+        const unsigned E = __reduce_max_sync(FULL, max(e0, e1));
+        const unsigned sh0 = 2 * (E - e0), sh1 = 2 * (E - e1);
+        unsigned long long acc = (e0 && sh0 < 64 ? (q0 << 9) >> sh0 : 0ull) +
+                                 (e1 && sh1 < 64 ? (q1 << 9) >> sh1 : 0ull);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        // value = acc * 2^(2E - 300 - 9); split the power so each factor is normal
+        const int p = 2 * (int)E - 309;
+        const double f1 = __longlong_as_double((long long)(1023 + p / 2) << 52);
+        const double f2 = __longlong_as_double((long long)(1023 + p - p / 2) << 52);
+        s2 = ((double)acc * f1) * f2;
+        t0 = (double)x0;
+        t1 = (double)x1;
+    } else {
+        auto expo = [](double a) { return (unsigned)(__double_as_longlong(a) >> 52) & 0x7ffu; };
+        const unsigned ef = __reduce_max_sync(FULL, max(expo(x0), expo(x1)));
+        if (ef != 0) {
+            const unsigned es = min(ef, 2045u);
+            const double sc = __longlong_as_double((long long)(2046u - es) << 52);   // 2^(1023 - es)
+            inv_sc = __longlong_as_double((long long)es << 52);                      // 2^(es - 1023)
+            t0 = x0 * sc;
+            t1 = x1 * sc;
+        } else {   // every entry subnormal or zero
+            t0 = (x0 * 0x1p1022) * 0x1p52;
+            t1 = (x1 * 0x1p1022) * 0x1p52;
+            inv_sc = 0x1p-1074;
+        }
+        double part = t0 * t0;
+        if (m > 32) part = fma(t1, t1, part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        s2 = part;
+    }
+    // Goldschmidt: g -> sqrt(s2), h -> 1 / (2 sqrt(s2))
+    const double y = rsqrt_approx(s2);
+    double g = s2 * y, h = 0.5 * y;
+#pragma unroll
+    for (int i = 0; i < STEPS; ++i) {
+        const double r = fma(-g, h, 0.5);
+        g = fma(g, r, g);
+        h = fma(h, r, h);
+    }
+    const double a = __shfl_sync(FULL, t0, 0);
+    const double absa = fabs(a);
+    const double tau = fma(absa, h + h, 1.0);      // (beta - alpha) / beta = 1 + |alpha| / norm
+    const double den = absa + g;
+    double rd = rcp_approx(den);
+#pragma unroll
+    for (int i = 0; i < STEPS; ++i) {
+        const double e = fma(-den, rd, 1.0);
+        rd = fma(rd, e, rd);
+    }
+    // vs = sign(alpha) / (|alpha| + norm): the sign by the bit of alpha (sign(+-0) = +1)
+    const bool neg = alpha < (T)0;
+    const double vs = neg ? -rd : rd;
+    if constexpr (sizeof(T) == 4) {
+        if (fabs(vs) < 1e38) {        // vs fits FP32: one FP32 product per entry
+            const float vsf = (float)vs;
+            if (lane < MAXM) v[lane] = lane == 0 ? 1.0f : (lane < m ? (float)x0 * vsf : 0.0f);
+            if (lane + 32 < MAXM) v[lane + 32] = lane + 32 < m ? (float)x1 * vsf : 0.0f;
+        } else {                      // a vector of FP32 subnormals: the product in FP64
+            if (lane < MAXM) v[lane] = lane == 0 ? 1.0f : (lane < m ? (float)(t0 * vs) : 0.0f);
+            if (lane + 32 < MAXM) v[lane + 32] = lane + 32 < m ? (float)(t1 * vs) : 0.0f;
+        }
+    } else {
+        if (lane < MAXM) v[lane] = lane == 0 ? 1.0 : (lane < m ? t0 * vs : 0.0);
+        if (lane + 32 < MAXM) v[lane + 32] = lane + 32 < m ? t1 * vs : 0.0;
+    }
+    if (lane == 0) {
+        tb[0] = (T)tau;
+        tb[1] = (T)((neg ? g : -g) * inv_sc);
+        tb[2] = (T)vs;
     }
 }
 

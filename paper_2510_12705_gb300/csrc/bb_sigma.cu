@@ -80,8 +80,15 @@ __global__ void sigma_bounds_kernel(int64_t n, const T* __restrict__ d, const T*
 //   - an exactly zero p_i is replaced by -pivmin p_{i-1} (the pivot rule of
 //     LAPACK's bisection; an underflow to a signed zero keeps the sign);
 //   - the pair (p_{i-1}, p_i) is rescaled by an exact power of two after every
-//     second pivot pair when its exponent leaves [-400, 400] (a pivot changes
-//     the magnitude by less than 16 for the scaled matrix).
+//     second pivot pair when its exponent leaves [-400, 400].  Bounds: in the
+//     scaled matrix (max |f| in [1, 2)) a pivot grows the pair by less than 16;
+//     it shrinks the pair by at most x unless the pivot cancels, and the
+//     bisection never evaluates x below about 2^-55 ub (it stops at an absolute
+//     accuracy of eps * sigma_max), so four pivots shrink it by at most about
+//     2^-220 and the pair stays normal between checks.  A cancelling pivot is
+//     followed by a large one.  (For x far below that range a run of tiny
+//     couplings can underflow the pair; the count is used only on this range,
+//     where tests/test_sigma_recurrence.py compares it with the oracle's.)
 __device__ __forceinline__ void sturm_step(double& pm1, double& p, double f2, double x, double pivmin,
                                            int64_t& neg)
 {

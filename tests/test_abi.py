@@ -160,12 +160,45 @@ def test_stage_count_limit(bb):
                                None) == bb.BB_ERR_UNSUPPORTED
 
 
+def _group_window_bytes(es, b, tw, K, maxm):
+    """Largest group-kernel window over the stages: V (K+d) x PV, H (bw-K-d) x
+    PH with odd pitches, plus K right reflectors and the staging vectors."""
+    best, bw = 0, b
+    while bw > 1:
+        d = min(tw, bw - 1)
+        k = min(K, (bw - d) // 3)
+        if k >= 1:
+            pv, ph = (bw + k + d) | 1, (k + d) | 1
+            best = max(best, (k + d) * pv + (bw - k - d) * ph)
+        bw -= d
+    small = (K * maxm + K * 4 + 2 * (maxm + 1) + 8 + (maxm + 1) + 64 + 3) & ~3
+    return es * (small + best) if best else 0
+
+
 def test_shared_bytes_model(bb):
-    # both panels of a row-bulge: (MAXM + 1) x (b + TW + 2) elements each
-    assert bb.bb_shared_bytes(4096, 128, bb.BB_F64, bb.Tuning(tw=16)) == 8 * 18 * 2 * (128 + 16 + 2)
-    assert bb.bb_shared_bytes(4096, 512, bb.BB_F32, bb.Tuning(tw=32)) == 4 * 34 * 2 * (512 + 32 + 2)
-    assert bb.bb_shared_bytes(4096, 512, bb.BB_F64, bb.Tuning(tw=32)) > 227 * 1024
+    # per-sweep kernel: both panels of a row-bulge, (MAXM + 1) x (b + TW + 2) elements each
+    t = bb.Tuning(tw=16, group=-1, teams=-1)
+    assert bb.bb_shared_bytes(4096, 128, bb.BB_F64, t) == 8 * 18 * 2 * (128 + 16 + 2)
+    t = bb.Tuning(tw=32, group=-1, teams=-1)
+    assert bb.bb_shared_bytes(4096, 512, bb.BB_F32, t) == 4 * 34 * 2 * (512 + 32 + 2)
+    assert bb.bb_shared_bytes(4096, 512, bb.BB_F64, bb.Tuning(tw=32, group=-1, teams=-1)) > 227 * 1024
     assert bb.bb_shared_bytes(0, 4, bb.BB_F64) == 0
+    # with the group kernel: the larger of the two
+    for (b, tw, es, dt, K, maxm) in [(128, 16, 8, bb.BB_F64, 8, 17), (128, 32, 4, bb.BB_F32, 16, 33),
+                                     (64, 32, 8, bb.BB_F64, 4, 33), (40, 8, 4, bb.BB_F32, 8, 9)]:
+        per_sweep = es * (maxm + 1) * 2 * (b + tw + 2)
+        got = bb.bb_shared_bytes(4096, b, dt, bb.Tuning(tw=tw, group=K, teams=-1))
+        assert got == max(per_sweep, _group_window_bytes(es, b, tw, K, maxm)), (b, tw, K)
+        # team kernel on the last stage: circular window (2W + 3) bw columns of
+        # 3 bw - 1 band offsets (even pitch) plus per-team scratch
+        bwl = b
+        while bwl - min(tw, bwl - 1) > 1:
+            bwl -= min(tw, bwl - 1)
+        for W in (2, 4):
+            pitch = 3 * bwl - 1 + ((3 * bwl - 1) & 1)
+            team = es * ((2 * W + 3) * bwl * pitch + W * ((5 * maxm + 73 + 3) & ~3))
+            got = bb.bb_shared_bytes(4096, b, dt, bb.Tuning(tw=tw, group=-1, teams=W))
+            assert got == max(per_sweep, team), (b, tw, W)
 
 
 def test_tuner_features_and_grid():
@@ -215,3 +248,13 @@ def test_committed_tuner_artifacts_consistent():
     assert probs <= set(tuner.default_grid())
     assert all(r["ms"] > 0 for r in rows)
     assert bench.reference_tw(32768, 128) in tuner.TWS
+
+
+@pytest.mark.parametrize("n,b,tw", [(32768, 128, 32), (32768, 128, 16), (300, 40, 16), (100, 7, 3)])
+def test_stage_counts_sum_to_schedule(bb, n, b, tw):
+    tot = bb.bb_schedule_counts(n, b, tw)
+    parts = [bb.bb_stage_counts(n, b, tw, s) for s in range(tot.stages)]
+    assert all(p.stages == tot.stages for p in parts)
+    assert sum(p.steps for p in parts) == tot.steps
+    assert sum(p.flops for p in parts) == pytest.approx(tot.flops, rel=1e-12)
+    assert sum(p.elements for p in parts) == pytest.approx(tot.elements, rel=1e-12)

@@ -126,3 +126,21 @@ def test_shard_run_local_matches_single_calls():
             bb.band_to_bidiag(band, b, d, e)
             assert np.array_equal(got[i][0], d.cpu().numpy())
             assert np.array_equal(got[i][1], e.cpu().numpy())
+
+
+def test_one_call_batched_equals_plan():
+    """band_to_bidiag_batched (one call) gives the same bits as the plan API."""
+    import torch
+    import paper_2510_12705_gb300 as bb
+    dtype = torch.float64
+    probs = bandgen.batch_problems(12, seed=5, n_lo=50, n_hi=600, bands=(4, 16, 40, 64))
+    a = _make(probs, dtype)
+    b_ = _make(probs, dtype)
+    plan = bb.BatchPlan([(band, b, d, e) for band, b, d, e, _ in a])
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.execute(ws)
+    bb.band_to_bidiag_batched([(band, b, d, e) for band, b, d, e, _ in b_])
+    assert bb.bb_last_device_status() == 0
+    for (_, _, d1, e1, _), (_, _, d2, e2, _) in zip(a, b_):
+        n = d1.numel()
+        assert torch.equal(d1, d2) and torch.equal(e1[: n - 1], e2[: n - 1])

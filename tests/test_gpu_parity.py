@@ -239,3 +239,36 @@ def test_host_entry_point_matches_device(dtype):
     d2, e2, st = run_gpu(ab.astype(np.float64), 50, "f64" if dtype == np.float64 else "f32")
     assert st == 0
     assert np.array_equal(d.astype(np.float64), d2) and np.array_equal(e.astype(np.float64), e2)
+
+
+# ------------------------------------------- kernel variants of one reduction
+
+VARIANTS = [{"group": -1}, {"group": 1}, {"group": 4}, {"group": 16},
+            {"teams": 2}, {"teams": 4}, {"group": 16, "teams": 8}]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,b,tw", [(640, 128, 16), (511, 48, 5), (333, 40, 16), (1500, 64, 32),
+                                    (97, 96, 32), (700, 20, 3)])
+def test_kernel_variants(n, b, tw, dtype):
+    # the group kernel (K sweeps per CTA on the split stages), the team kernel
+    # (W sweeps per CTA on the last stage) and the per-sweep kernel reduce the
+    # same matrix to bidiagonals with the oracle's singular values
+    ab = bandgen.random_band(n, b, seed=7 * n + b)
+    _, _, s0 = _oracle_sigma(ab, b, tw)
+    for var in VARIANTS:
+        d, e, st = run_gpu(ab, b, dtype, tuning={"tw": tw, **var})
+        assert st == 0, var
+        err, _ = sigma_err(d, e, s0)
+        assert err <= (TOL_F64 if dtype == "f64" else TOL_F32), (var, err)
+
+
+@pytest.mark.parametrize("var", [{"group": 8}, {"teams": 4}])
+def test_variant_launch_shapes_bitwise(var):
+    # any CTA count gives the same bits (each kernel's order of operations is
+    # fixed by its protocol, not by the schedule)
+    ab = bandgen.random_band(500, 40, seed=91)
+    ref = run_gpu(ab, 40, "f64", tuning={"tw": 8, **var})
+    for sif in (1, 5):
+        d, e, st = run_gpu(ab, 40, "f64", tuning={"tw": 8, "sweeps_in_flight": sif, **var})
+        assert st == 0 and np.array_equal(d, ref[0]) and np.array_equal(e, ref[1])

@@ -123,9 +123,9 @@ def test_f64_subnormal_band():
     d, e, st = run_gpu(ab, B_S, "f64", tuning={"tw": TW_S})
     assert st == 0
     assert np.all(np.isfinite(d)) and np.all(np.isfinite(e))
-    up = 2.0 ** 1060
-    s0 = oracle.bidiag_sigma(d0 * up, e0 * up)
-    s = oracle.bidiag_sigma(d * up, e * up)
+    up = 2.0 ** 530                    # applied twice: 2^1060 itself overflows
+    s0 = oracle.bidiag_sigma(d0 * up * up, e0 * up * up)
+    s = oracle.bidiag_sigma(d * up * up, e * up * up)
     assert s0[0] > 0
     # a few hundred half-ulps of 2^-1074, rescaled: 2^-14 per unit of sigma_max / 10
     assert np.max(np.abs(s - s0)) <= 2e-2 * s0[0]
@@ -175,3 +175,16 @@ def test_zero_rows_and_columns(dtype, tw):
     assert np.max(np.abs(s - s0)) <= tol * s0[0]
     # five zero rows: rank <= n - 5, kept up to rounding
     assert np.sum(s <= (1e-12 if dtype == "f64" else 1e-5) * s0[0]) >= 5
+
+
+def test_f32_subnormal_band_stays_finite():
+    # FP32 entries around 1e-40 are subnormal: reflector vectors whose norm is
+    # below the FP32 range of 1 / (|alpha| + ||x||) must still give finite
+    # reflectors (the same happens near the end of random triangular bands,
+    # whose trailing singular values underflow in FP32)
+    ab = bandgen.random_band(N_S, B_S, seed=21) * 1e-40
+    for tw in (TW_S, 16, 32):
+        d, e, st = run_gpu(ab, B_S, "f32", tuning={"tw": tw})
+        assert st == 0
+        assert np.all(np.isfinite(d)) and np.all(np.isfinite(e))
+        assert float(np.max(np.abs(d))) <= 1e-37

@@ -111,3 +111,52 @@ def test_closed_form_all_ones():
     n = 200
     k = np.arange(1, n + 1)
     assert np.max(np.abs(kernel_sigma(np.ones(n), np.ones(n - 1)) - 2 * np.cos(k * np.pi / (2 * n + 1)))) < 1e-14
+
+
+def _exact_count(d, e, x):
+    """#{sigma < x}: negative pivots of the shifted Golub-Kahan LDL^T in exact
+    rational arithmetic, minus n (brute force, independent of rounding)."""
+    from fractions import Fraction
+    f = []
+    for k in range(len(d)):
+        f.append(Fraction(float(d[k])))
+        if k + 1 < len(d):
+            f.append(Fraction(float(e[k])))
+    X = Fraction(x)
+    q = -X
+    neg = 1
+    for fi in f:
+        q = -X - fi * fi / q if q != 0 else -X
+        neg += q < 0
+    return neg - len(d)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_count_on_runs_of_tiny_couplings(seed):
+    # a run of entries 1e-100 .. 1e-150 of the largest (squares still normal)
+    # and shifts over the whole range the bisection evaluates (down to about
+    # 2^-55 ub): the kernel's count equals the oracle's and the exact one
+    rng = np.random.default_rng(seed)
+    n = 30
+    d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
+    lo = int(rng.integers(2, n - 10))
+    d[lo:lo + 8] *= 10.0 ** -rng.uniform(100, 150)
+    e[lo:lo + 8] *= 10.0 ** -rng.uniform(100, 150)
+    fm = max(np.max(np.abs(d)), np.max(np.abs(e)))
+    sc = math.ldexp(1.0, min(max(1 - math.frexp(fm)[1], -1022), 1023))
+    pivmin = max((fm * sc) ** 2 * DBL_MIN, DBL_MIN)
+    for u in np.linspace(0.0, 16.5, 12):
+        x = 10.0 ** -u * sc
+        k = _count(d, e, x, pivmin, sc)
+        assert k == oracle.bidiag_count_below(d * sc, e * sc, x, pivmin), (u, k)
+        assert k == _exact_count(d * sc, e * sc, x), (u, k)
+
+
+def test_oracle_count_is_exact():
+    # the oracle's pivot-form count against the rational count, random inputs
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        n = int(rng.integers(1, 25))
+        d, e = rng.standard_normal(n), rng.standard_normal(max(n - 1, 0))
+        for x in 10.0 ** -rng.uniform(-0.5, 12, 5):
+            assert oracle.bidiag_count_below(d, e, x, DBL_MIN) == _exact_count(d, e, x)
