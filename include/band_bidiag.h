@@ -288,10 +288,13 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
  * the caller first).  Method: one thread per
  * singular value, bisection on the Sturm count of the Golub-Kahan matrix
  * (order 2n, zero diagonal, off-diagonal d0, e0, d1, e1, ...; three-term
- * recurrence without divisions, restarted at splits), to an
+ * recurrence without divisions on the squared couplings, computed once,
+ * restarted at splits), started from a shared grid of counts over
+ * [0, sigma bound] (about n/4 cells, at most 2^14), to an
  * absolute accuracy of about eps * sigma_max (the FP64 resolution for the
  * largest values).  Cost O(n^2 log(1/eps)); asynchronous
- * on `stream`.  workspace: device, >= bb_bidiag_sigma_workspace_size(n) bytes,
+ * on `stream`.  workspace: device, >= bb_bidiag_sigma_workspace_size(n) bytes
+ * (66048 + 16 n: bounds, grid counts and the 2n - 1 squared couplings),
  * 16-byte aligned.  Returns BB_OK, BB_ERR_ARG (n < 1, NULL pointers, dtype),
  * BB_ERR_WORKSPACE, BB_ERR_UNSUPPORTED (n >= 2^31) or BB_ERR_LAUNCH.
  */

@@ -13,6 +13,7 @@
 // power-of-two rescaling, restarts at splits, LAPACK's zero-pivot rule.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
@@ -72,15 +73,31 @@ __global__ void sigma_bounds_kernel(int64_t n, const T* __restrict__ d, const T*
     }
 }
 
+// f2[i] = (sc f_i)^2, i < 2n - 1: the squared couplings of the scaled
+// Golub-Kahan matrix, computed once for all the counts.
+template <typename T>
+__global__ void sigma_squares_kernel(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
+                                     const double* __restrict__ bounds, double* __restrict__ f2)
+{
+    const double sc = bounds[2];
+    const int64_t m = 2 * n - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double fi = ((i & 1) ? (double)e[i >> 1] : (double)d[i >> 1]) * sc;
+        f2[i] = fi * fi;
+    }
+}
+
 // #{sigma < x} for x > 0: the sign changes of the Sturm sequence p_0 = 1,
 // p_1 = -x, p_i = -x p_{i-1} - f_{i-1}^2 p_{i-2} (the LDL^T pivots are
 // q_i = p_i / p_{i-1}; a sign change is a negative pivot).  In this form a
-// pivot costs one FMA on the dependent chain and no division.
+// pivot costs one multiply and one FMA on the FP64 pipe and no division; the
+// tests on zero and the exponent checks are integer operations on the bits.
 //   - f_{i-1}^2 == 0 splits the matrix: the sequence restarts (q_i = -x < 0);
 //   - an exactly zero p_i is replaced by -pivmin p_{i-1} (the pivot rule of
 //     LAPACK's bisection; an underflow to a signed zero keeps the sign);
 //   - the pair (p_{i-1}, p_i) is rescaled by an exact power of two after every
-//     second pivot pair when its exponent leaves [-400, 400].  Bounds: in the
+//     fourth pivot when its exponent leaves [-400, 400].  Bounds: in the
 //     scaled matrix (max |f| in [1, 2)) a pivot grows the pair by less than 16;
 //     it shrinks the pair by at most x unless the pivot cancels, and the
 //     bisection never evaluates x below about 2^-55 ub (it stops at an absolute
@@ -89,26 +106,31 @@ __global__ void sigma_bounds_kernel(int64_t n, const T* __restrict__ d, const T*
 //     followed by a large one.  (For x far below that range a run of tiny
 //     couplings can underflow the pair; the count is used only on this range,
 //     where tests/test_sigma_recurrence.py compares it with the oracle's.)
-__device__ __forceinline__ void sturm_step(double& pm1, double& p, double f2, double x, double pivmin,
-                                           int64_t& neg)
+__device__ __forceinline__ void sturm_step(double& pm1, double& p, double f2, double mx, double pivmin,
+                                           unsigned& neg)
 {
-    if (f2 == 0.0) {
+    if (__double_as_longlong(f2) == 0) {        // f2 >= +0 always
         pm1 = 1.0;
-        p = -x;
+        p = mx;
         neg += 1;
         return;
     }
-    double pn = fma(-x, p, -(f2 * pm1));
-    if (pn == 0.0) pn = (p != 0.0) ? -pivmin * p : -pivmin;
-    neg += ((__double_as_longlong(pn) ^ __double_as_longlong(p)) < 0);   // sign change
+    double pn = fma(mx, p, -(f2 * pm1));
+    long long pb = __double_as_longlong(pn);
+    if ((pb << 1) == 0) {                       // +-0
+        pn = (__double_as_longlong(p) << 1) != 0 ? -pivmin * p : -pivmin;
+        pb = __double_as_longlong(pn);
+    }
+    neg += (unsigned)((pb ^ __double_as_longlong(p)) < 0);   // sign change
     pm1 = p;
     p = pn;
 }
 
 __device__ __forceinline__ void sturm_rescale(double& pm1, double& p)
 {
-    const double m = fmax(fabs(pm1), fabs(p));
-    const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1023;   // -1023 for 0 / subnormal
+    const int e1 = (int)((__double_as_longlong(pm1) >> 52) & 0x7ff);
+    const int e2 = (int)((__double_as_longlong(p) >> 52) & 0x7ff);
+    const int ex = max(e1, e2) - 1023;          // exponent of max(|pm1|, |p|); -1023 for 0 / subnormal
     if (ex > 400 || ex < -400) {
         const double s = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, finite
         pm1 *= s;
@@ -116,49 +138,84 @@ __device__ __forceinline__ void sturm_rescale(double& pm1, double& p)
     }
 }
 
-template <typename T>
-__device__ __forceinline__ int64_t count_below(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
-                                               double x, double pivmin, double sc)
+// #{sigma < x} from the squared couplings f2[0 .. 2n-2]
+__device__ __forceinline__ unsigned count_below(int64_t n, const double* __restrict__ f2, double x,
+                                                double pivmin)
 {
-    double pm1 = 1.0, p = -x;    // p_0, p_1
+    const double mx = -x;
+    double pm1 = 1.0, p = mx;    // p_0, p_1
     if (fabs(p) < pivmin) p = -pivmin;
-    int64_t neg = 1;             // p_0 > 0 > p_1
-    for (int64_t k = 0; k < n; ++k) {
-        // f_{2k} = d_k, then f_{2k+1} = e_k (absent after d_{n-1})
-        const double dk = (double)__ldg(d + k) * sc;
-        sturm_step(pm1, p, dk * dk, x, pivmin, neg);
-        if (k + 1 < n) {
-            const double ek = (double)__ldg(e + k) * sc;
-            sturm_step(pm1, p, ek * ek, x, pivmin, neg);
-        }
-        if (k & 1) sturm_rescale(pm1, p);
+    unsigned neg = 1;            // p_0 > 0 > p_1
+    const int64_t m = 2 * n - 1;
+    int64_t i = 0;
+    for (; i + 4 <= m; i += 4) {
+        const double a0 = __ldg(f2 + i), a1 = __ldg(f2 + i + 1), a2 = __ldg(f2 + i + 2),
+                     a3 = __ldg(f2 + i + 3);
+        sturm_step(pm1, p, a0, mx, pivmin, neg);
+        sturm_step(pm1, p, a1, mx, pivmin, neg);
+        sturm_step(pm1, p, a2, mx, pivmin, neg);
+        sturm_step(pm1, p, a3, mx, pivmin, neg);
+        sturm_rescale(pm1, p);
     }
-    return neg - n;
+    for (; i < m; ++i) sturm_step(pm1, p, __ldg(f2 + i), mx, pivmin, neg);
+    return neg - (unsigned)n;
+}
+
+// cnt[k] = #{sigma < ub k / G}, k = 1 .. G-1 (cnt[0] = 0, cnt[G] = n): a
+// shared first cut of [0, ub] that replaces the first log2(G) halvings of
+// every value's bisection
+__global__ void sigma_grid_kernel(int64_t n, const double* __restrict__ f2, const double* __restrict__ bounds,
+                                  int G, unsigned* __restrict__ cnt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > G) return;
+    if (k == 0) { cnt[0] = 0; return; }
+    if (k == G) { cnt[G] = (unsigned)n; return; }
+    cnt[k] = count_below(n, f2, bounds[0] * ((double)k / (double)G), bounds[1]);
 }
 
 // thread j: the (j+1)-th smallest singular value, written to sigma[n-1-j]
 // (descending order, like LAPACK's xBDSQR)
-template <typename T>
-__global__ void sigma_bisect_kernel(int64_t n, const T* __restrict__ d, const T* __restrict__ e,
-                                    const double* __restrict__ bounds, double* __restrict__ sigma)
+__global__ void sigma_bisect_kernel(int64_t n, const double* __restrict__ f2, const double* __restrict__ bounds,
+                                    int G, const unsigned* __restrict__ cnt, double* __restrict__ sigma)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const double ub = bounds[0], pivmin = bounds[1], sc = bounds[2], isc = bounds[3];
-    double lo = 0.0, hi = ub;
+    const double ub = bounds[0], pivmin = bounds[1], isc = bounds[3];
+    // first cut: grid cell [ub k / G, ub (k+1) / G] with cnt[k] <= j < cnt[k+1]
+    // (a search that keeps exactly that invariant, valid even if the computed
+    // counts were not monotone)
+    int klo = 0, khi = G;
+    while (khi - klo > 1) {
+        const int km = (klo + khi) >> 1;
+        if ((int64_t)__ldg(cnt + km) <= j) klo = km; else khi = km;
+    }
+    double lo = klo == 0 ? 0.0 : ub * ((double)klo / (double)G);
+    double hi = khi == G ? ub : ub * ((double)khi / (double)G);
     // invariant: #{sigma < lo} <= j < #{sigma < hi}.  Stop at the FP64
     // resolution around the value or at the absolute accuracy eps * ub (the
     // accuracy of any backward-stable bidiagonal SVD, and what bisection can
-    // guarantee for values far below sigma_max): at most ~55 halvings
+    // guarantee for values far below sigma_max): at most ~55 halvings in all
     const double abs_tol = 0.5 * DBL_EPSILON * ub;
     for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
         if (hi - lo <= fmax(2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)), abs_tol) + 2.0 * pivmin) break;
-        if (count_below(n, d, e, mid, pivmin, sc) > j) hi = mid; else lo = mid;
+        if ((int64_t)count_below(n, f2, mid, pivmin) > j) hi = mid; else lo = mid;
     }
     sigma[n - 1 - j] = (0.5 * (lo + hi)) * isc;
 }
+
+// grid size: a power of two, about half a count per singular value, at most 2^14
+int grid_cells(int64_t n)
+{
+    int G = 1;
+    while (G < 16384 && 4 * (int64_t)G <= n) G <<= 1;
+    return G;
+}
+
+constexpr size_t kCntOffset = 256;
+constexpr size_t kF2Offset = kCntOffset + 4 * (16384 + 1 + 63);   // 66048, 256-byte aligned
 
 }  // namespace
 
@@ -166,8 +223,8 @@ extern "C" {
 
 size_t bb_bidiag_sigma_workspace_size(int64_t n)
 {
-    (void)n;
-    return 256;
+    // bounds (256 B) | grid counts | squared couplings (2n doubles)
+    return kF2Offset + (size_t)(n > 0 ? n : 0) * 16;
 }
 
 int bb_bidiag_sigma(int64_t n, int dtype, const void* d, const void* e, double* sigma_out,
@@ -179,17 +236,23 @@ int bb_bidiag_sigma(int64_t n, int dtype, const void* d, const void* e, double* 
     if (!workspace || ws_bytes < bb_bidiag_sigma_workspace_size(n) || ((uintptr_t)workspace & 15))
         return BB_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    double* bounds = (double*)workspace;
-    // one warp per block: each thread is a long dependent FP64 chain, so
-    // spreading the values over all SMs beats packing warps onto a few
-    const unsigned grid = (unsigned)((n + 31) / 32);
+    unsigned char* ws = (unsigned char*)workspace;
+    double* bounds = (double*)ws;
+    unsigned* cnt = (unsigned*)(ws + kCntOffset);
+    double* f2 = (double*)(ws + kF2Offset);
+    const int G = grid_cells(n);
+    const unsigned sq_grid = (unsigned)std::min<int64_t>((2 * n - 1 + 255) / 256, 1184);
     if (dtype == BB_F64) {
         sigma_bounds_kernel<double><<<1, 1024, 0, st>>>(n, (const double*)d, (const double*)e, bounds);
-        sigma_bisect_kernel<double><<<grid, 32, 0, st>>>(n, (const double*)d, (const double*)e, bounds, sigma_out);
+        sigma_squares_kernel<double><<<sq_grid, 256, 0, st>>>(n, (const double*)d, (const double*)e, bounds, f2);
     } else {
         sigma_bounds_kernel<float><<<1, 1024, 0, st>>>(n, (const float*)d, (const float*)e, bounds);
-        sigma_bisect_kernel<float><<<grid, 32, 0, st>>>(n, (const float*)d, (const float*)e, bounds, sigma_out);
+        sigma_squares_kernel<float><<<sq_grid, 256, 0, st>>>(n, (const float*)d, (const float*)e, bounds, f2);
     }
+    // one warp per block: each thread is a long dependent FP64 chain, so
+    // spreading the work over all SMs beats packing warps onto a few
+    sigma_grid_kernel<<<(unsigned)((G + 1 + 31) / 32), 32, 0, st>>>(n, f2, bounds, G, cnt);
+    sigma_bisect_kernel<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(n, f2, bounds, G, cnt, sigma_out);
     return cudaGetLastError() == cudaSuccess ? BB_OK : BB_ERR_LAUNCH;
 }
 

@@ -128,7 +128,8 @@ def test_tuning_entry_points_host_checks(bb):
 def test_bidiag_sigma_host_checks(bb):
     L = bb.lib()
     ws = bb.lib().bb_bidiag_sigma_workspace_size(100)
-    assert ws >= 16
+    # bounds + grid counts (66048 B) + 2n doubles of squared couplings
+    assert ws == 66048 + 16 * 100
     # validation happens before any CUDA call
     assert L.bb_bidiag_sigma(0, 1, 16, 16, 16, 256, ws, None) == bb.BB_ERR_ARG
     assert L.bb_bidiag_sigma(10, 7, 16, 16, 16, 256, ws, None) == bb.BB_ERR_ARG

@@ -1,6 +1,6 @@
 """Host model of the GPU singular-value count (division-free three-term Sturm
 recurrence on the Golub-Kahan matrix, restarted at splits, power-of-two
-rescaling), replayed in Python with the kernel's rules and compared with the
+rescaling, bisection started from a shared grid of counts), replayed in Python with the kernel's rules and compared with the
 oracle's bisection on the inputs that stress it: exact zeros (splits), tiny
 and huge entries, the all-ones closed form."""
 import math
@@ -57,9 +57,23 @@ def kernel_sigma(d, e):
     fp = np.concatenate([[0.0], f[:-1]])
     ub = 2 * float(np.max(0.5 * np.abs(f) + 0.5 * np.abs(fp))) * sc * (1 + 4 * EPS) + DBL_MIN
     pivmin = max((fm * sc) ** 2 * DBL_MIN, DBL_MIN)
+    # shared first cut: counts at ub k / G, G a power of two with 4 G <= n
+    # (at most 2^14); each value starts from the cell that brackets it
+    G = 1
+    while G < 16384 and 4 * G <= n:
+        G *= 2
+    cnt = [0] + [_count(d, e, ub * (k / G), pivmin, sc) for k in range(1, G)] + [n]
     out = np.empty(n)
     for j in range(n):
-        lo, hi = 0.0, ub
+        klo, khi = 0, G
+        while khi - klo > 1:
+            km = (klo + khi) // 2
+            if cnt[km] <= j:
+                klo = km
+            else:
+                khi = km
+        lo = 0.0 if klo == 0 else ub * (klo / G)
+        hi = ub if khi == G else ub * (khi / G)
         for _ in range(200):
             mid = 0.5 * (lo + hi)
             if mid <= lo or mid >= hi:
