@@ -71,7 +71,10 @@ extern "C" {
  *   tw               inner tilewidth TW: bandwidth removed per stage (1..32)
  *   tpb              threads per bulge (CTA size: 64, 128, 256 or 512)
  *   sweeps_in_flight persistent CTAs, i.e. sweeps processed concurrently
- *                    (the paper's "max blocks"); capped at what fits on the GPU
+ *                    (the paper's "max blocks"); capped at what fits on the GPU.
+ *                    0 = every CTA that fits, except for FP64 stages of the
+ *                    group kernel whose sweeps have at most 3 x (SM count)
+ *                    row-bulges: one CTA per SM there
  *   flags            BB_FLAG_*
  *   timeout_s        limit on every device spin-wait without progress, seconds
  *                    (default 5 s)
@@ -79,8 +82,9 @@ extern "C" {
  *                    call's stream immediately before and after the persistent
  *                    bulge-chasing kernels, so a caller can time them alone
  *   group            sweeps one CTA chases together through shared memory (the
- *                    paper's "max blocks" unrolled into one block): 0 = default,
- *                    -1 = one sweep per CTA on every stage, k >= 1 = at most k.
+ *                    paper's "max blocks" unrolled into one block): 0 = default
+ *                    (24), -1 = one sweep per CTA on every stage, k >= 1 = at
+ *                    most k (fewer when the window would not fit shared memory).
  *                    A stage (bw -> bw - d) takes min(k, (bw - d) / 3) sweeps per
  *                    CTA; other stages but the last run one sweep per CTA.
  *   teams            sweeps one CTA runs side by side on the last stage (the one

@@ -100,14 +100,6 @@ __global__ void extract_kernel(Launch L)
 // entries [p*H, p*H+H); one shuffle combines their partial dot products).
 template <int MAXM> struct Split { static constexpr int H = (MAXM + 1) / 2; };
 
-__device__ __forceinline__ void bar_arrive(int id, int n)
-{
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_sync_n(int id, int n)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 
 // e / div for 0 <= e < 2^22, div >= 1, via an FP32 reciprocal plus correction
 __device__ __forceinline__ int fast_div(int e, int div, float inv)
@@ -506,7 +498,7 @@ int maxm_for(int tw)
 }
 
 // sweeps per CTA of the group kernel when the tuning leaves it open
-constexpr int kDefaultGroup = 8;
+constexpr int kDefaultGroup = 24;
 // sweeps per CTA of the team kernel (last stage) when the tuning leaves it
 // open: 0, the per-sweep kernel runs the last stage unless a tuning asks for
 // the team kernel (it is slower than the per-sweep kernel as it stands)
@@ -561,9 +553,9 @@ struct LaunchPlan {
 };
 
 // Dynamic shared memory of the group kernel with at most K sweeps per CTA:
-// the largest window over the stages and problems it takes (0 when it takes
-// none).
-size_t group_smem_bytes(const LaunchPlan& P, int K)
+// the largest window over the problems it takes on `stage` (every stage when
+// stage < 0); 0 when it takes none.
+size_t group_smem_bytes(const LaunchPlan& P, int K, int stage = -1)
 {
     if (K < 1) return 0;
     const int tw = P.tune.tw, maxm = maxm_for(tw);
@@ -571,6 +563,7 @@ size_t group_smem_bytes(const LaunchPlan& P, int K)
     int window = 0;
     for (const Desc& D : P.descs)
         for (int st = 0; st < D.nstages; ++st) {
+            if (stage >= 0 && st != stage) continue;
             const int bw = D.b - st * tw, d = std::min(tw, bw - 1);
             const int k = group_members(bw, d, K);
             if (k >= 1) window = std::max(window, group_window_elems(bw, d, k));
@@ -703,10 +696,11 @@ int stage_tpb(int bw, int d, int user_tpb)
 
 // threads of the group kernel for a stage: 16 panel rows / columns per warp
 // and pass, one pass over the left reflector's columns
-// (at most 384: the kernel is compiled for two CTAs of 384 threads per SM)
+// (at most 384: the kernel is compiled for two CTAs of 384 threads per SM; at
+// least 128: its three warp teams need four warps)
 int group_tpb(int bw, int d, int user_tpb)
 {
-    if (user_tpb > 0) return std::min(user_tpb, 384);
+    if (user_tpb > 0) return std::max(128, std::min(user_tpb, 384));
     const int warps = (bw + d + 1 + 15) / 16;
     return std::max(128, std::min(384, 32 * warps));
 }
@@ -750,7 +744,7 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
         // widest stage bandwidth over the problems of each kernel, and the
         // tasks (problems x groups) of the group and team kernels
         int bw_max = 0, d_max = 0, gbw_max = 0, gd_max = 0;
-        int64_t gtasks = 0, ttasks = 0;
+        int64_t gtasks = 0, ttasks = 0, gsteps = 0;
         bool any_sweep = false;
         for (const Desc& D : P.descs)
             if (stage < D.nstages) {
@@ -761,6 +755,7 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
                     gd_max = std::max(gd_max, d);
                     const int nact = D.n - 1 - (bw - d);
                     gtasks = std::max<int64_t>(gtasks, nact > 0 ? (nact + k - 1) / k : 0);
+                    gsteps = std::max<int64_t>(gsteps, nact > 0 ? (D.n - 2 - (bw - d)) / bw + 1 : 0);
                 } else if (L.team && bw - d == 1) {
                     const int nact = D.n - 2;
                     ttasks = std::max<int64_t>(ttasks, nact > 0 ? (nact + L.team - 1) / L.team : 0);
@@ -776,7 +771,9 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
             const int tpb = which == 0 ? group_tpb(gbw_max, gd_max, P.tune.tpb)
                           : which == 1 ? 32 * (L.team + 1)
                                        : stage_tpb(bw_max, d_max, P.tune.tpb);
-            const size_t smem = which == 0 ? P.gsmem : which == 1 ? P.tsmem : P.smem;
+            // the group kernel's window is sized for this stage, so later
+            // (narrower) stages keep more CTAs per SM
+            const size_t smem = which == 0 ? group_smem_bytes(P, L.gK, stage) : which == 1 ? P.tsmem : P.smem;
             int per_sm = 0;
             const cudaError_t oe =
                 which == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gkern, tpb, smem)
@@ -791,6 +788,11 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
                            : which == 1 ? (int64_t)L.count * ttasks : L.total_tasks;
             int64_t grid = (int64_t)nsm * per_sm;
             if (P.tune.sif > 0) grid = std::min<int64_t>(grid, P.tune.sif);
+            else if (which == 0 && P.tune.dtype == BB_F64 && gsteps <= 3 * (int64_t)nsm)
+                // FP64 group steps keep an SM's FP64 pipe busy: while the
+                // stage's wavefront is short (few groups active at once) one
+                // CTA per SM runs each group step at the SM's full rate
+                grid = std::min<int64_t>(grid, nsm);
             grid = std::min<int64_t>(grid, LL.total_tasks);
             if (grid < 1) continue;
             if (!first && cudaMemsetAsync(&P.L.hdr->claim, 0, sizeof(int), st) != cudaSuccess)

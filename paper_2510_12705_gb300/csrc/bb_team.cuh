@@ -25,26 +25,6 @@
 
 namespace bb {
 
-__device__ __forceinline__ int ld_acquire_shared(const int* p)
-{
-    int v;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_relaxed_shared(const int* p)
-{
-    int v;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.relaxed.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_shared(int* p, int v)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-
 // One lane: spin until *p >= target (shared memory).  Gives up (sets the
 // error and abort words) when nothing changed for timeout_ns or another CTA
 // aborted.

@@ -163,7 +163,8 @@ def test_stage_count_limit(bb):
 
 def _group_window_bytes(es, b, tw, K, maxm):
     """Largest group-kernel window over the stages: V (K+d) x PV, H (bw-K-d) x
-    PH with odd pitches, plus K right reflectors and the staging vectors."""
+    PH with odd pitches, plus K right and K left reflectors (vectors and
+    {tau, beta, vs}) and the staging vector."""
     best, bw = 0, b
     while bw > 1:
         d = min(tw, bw - 1)
@@ -172,7 +173,7 @@ def _group_window_bytes(es, b, tw, K, maxm):
             pv, ph = (bw + k + d) | 1, (k + d) | 1
             best = max(best, (k + d) * pv + (bw - k - d) * ph)
         bw -= d
-    small = (K * maxm + K * 4 + 2 * (maxm + 1) + 8 + (maxm + 1) + 64 + 3) & ~3
+    small = (2 * K * maxm + 8 * K + (maxm + 1) + 64 + 3) & ~3
     return es * (small + best) if best else 0
 
 

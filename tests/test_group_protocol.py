@@ -6,13 +6,17 @@ Per group g (sweeps R0 = gK .. R0+K-1) and step s, with c = R0 + bw' + s bw:
   W1   wait: group g-1 completed step s
   LD1  load the window except the carried block and the tail columns
   U    right reflectors of every member, applied to the rows above c
-  ST1  store those rows;                     publish "step s upper done"
+  Ln   per member: right reflector on the rows >= c, left reflector on the
+       near columns c .. c+K+d-1 (the near warps; runs alongside ST1 .. LD2)
+  ST1  store the rows above c;               publish "step s upper done"
   W2   wait: group g-1 did the upper part of step s+1 (or finished)
   LD2  load the tail columns and the next step's carried block
-  L    per member: right reflector on the rows >= c, left reflector
+  Lf   per member: left reflector on the far columns >= c+K+d
   ST2  store everything but the carried block; publish "step s complete"
 (the last step stores the carried block too and publishes only once group
-g-1 has finished).
+g-1 has finished).  Ln is placed before ST1 here; in the kernel it overlaps
+ST1, W2 and LD2, which touch none of its cells (checked below: its cells are
+resident after LD1 and no other group reaches them before "step s complete").
 
 The model checks, for every stage of small matrices:
   * cross-group: every pair of operations of different groups that touch a
@@ -109,7 +113,10 @@ class Model:
         R0, kk = self.members(g)
         c = self.origin(g, s)
         act = [j for j in range(kk) if s < sweep_steps(n, bw, d, R0 + j)]
-        U, L = [], []
+        # near columns: c .. c+K+d-1 (the "near_wide" variant wrongly takes the
+        # tail columns too, before the wait that protects them)
+        xnear = c + self.K + d if self.variant != "near_wide" else c + bw + self.K + d
+        U, L, F = [], [], []
         for j in act:
             cj = c + j
             m = min(d + 1, n - cj)
@@ -127,12 +134,15 @@ class Model:
             lid = (R0 + j, s, "L")
             lgen = {(i, cj) for i in range(cj, cj + m)}
             lfull = {(i, x) for i in range(cj, cj + m) for x in range(cj, jmax + 1)}
-            L.append(("L", "L", lid, lgen, lfull))
+            L.append(("L", "L", lid, lgen, {(i, x) for (i, x) in lfull if x < xnear}))
+            far = {(i, x) for (i, x) in lfull if x >= xnear}
+            if far:
+                F.append(("F", "L", lid, lgen, far))
             self.full[rid] = full
             self.full[lid] = lfull
             self.gen[rid] = gen
             self.gen[lid] = lgen
-        return U + L
+        return U + L + F
 
     # ------------------------------------------------------------ schedule
     def run(self):
@@ -169,16 +179,17 @@ class Model:
                 wait(w1)
                 self.events.append((g, "LD", (s, "ld1", reg["ld1"]), dict(know)))
                 ops = self.ops(g, s)
-                for op in ops:
-                    if op[0] == "U":
-                        self.events.append((g, "OP", (s,) + op, dict(know)))
+                for phase in ("U", "L"):
+                    for op in ops:
+                        if op[0] == phase:
+                            self.events.append((g, "OP", (s,) + op, dict(know)))
                 self.events.append((g, "ST", (s, "st1", reg["st1"]), dict(know)))
                 publish(2 * s + 1)
                 if self.variant != "no_w2":
                     wait(2 * (s + 1) + 1 if s + 1 < Sp else 2 * Sp)
                 self.events.append((g, "LD", (s, "ld2", reg["ld2"]), dict(know)))
                 for op in ops:
-                    if op[0] == "L":
+                    if op[0] == "F":
                         self.events.append((g, "OP", (s,) + op, dict(know)))
                 st2 = set(reg["st2"])
                 if s == S - 1:
@@ -329,7 +340,7 @@ def test_group_protocol(n, b, tw, K):
     assert checked > 0
 
 
-@pytest.mark.parametrize("variant", ["weak_w1", "no_w2", "no_final_wait", "tail_late_only"])
+@pytest.mark.parametrize("variant", ["weak_w1", "no_w2", "no_final_wait", "tail_late_only", "near_wide"])
 def test_weakened_group_protocol_is_caught(variant):
     with pytest.raises(AssertionError):
         for (n, b, tw, K) in [(40, 12, 3, 2), (60, 16, 4, 3), (64, 24, 8, 4)]:
