@@ -88,10 +88,10 @@ extern "C" {
  *                    A stage (bw -> bw - d) takes min(k, (bw - d) / 3) sweeps per
  *                    CTA; other stages but the last run one sweep per CTA.
  *   teams            sweeps one CTA runs side by side on the last stage (the one
- *                    that ends at bandwidth 1), one warp each, on a shared-memory
- *                    window: 0 = default (one sweep per CTA), -1 = one sweep per
- *                    CTA, k >= 1 = at most k (fewer when the window would not
- *                    fit shared memory)
+ *                    that ends at bandwidth 1), a team of four warps each, on a
+ *                    shared-memory window: 0 = default (one sweep per CTA), -1 =
+ *                    one sweep per CTA, k >= 1 = at most min(k, 4) (fewer when
+ *                    the window would not fit shared memory)
  *   ev_launch/ev_count/launch_log  optional per-launch timing (NULL / 0 = none):
  *                    ev_launch is an array of ev_count cudaEvent_t handles;
  *                    launch i of the bulge-chasing kernels is bracketed by

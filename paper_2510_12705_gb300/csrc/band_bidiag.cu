@@ -535,7 +535,8 @@ bool resolve_tuning(int64_t n, int64_t b, int dtype, const bb_tuning* t, Resolve
     if (r->tpb != 0 && (r->tpb < 64 || r->tpb > 512 || r->tpb % 32 != 0)) return false;
     if (t && (t->group < -1 || t->teams < -1)) return false;
     if (r->group > 64) r->group = 64;
-    if (r->teams > 16) r->teams = 16;
+    if (r->teams > 4) r->teams = 4;          // teams of kTeamWarps warps, plus a data warp
+
     return true;
 }
 
@@ -769,7 +770,7 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
         for (int which = 0; which < 3; ++which) {
             if (which == 0 ? gtasks == 0 : which == 1 ? ttasks == 0 : !any_sweep) continue;
             const int tpb = which == 0 ? group_tpb(gbw_max, gd_max, P.tune.tpb)
-                          : which == 1 ? 32 * (L.team + 1)
+                          : which == 1 ? 32 * (L.team * kTeamWarps + 1)
                                        : stage_tpb(bw_max, d_max, P.tune.tpb);
             // the group kernel's window is sized for this stage, so later
             // (narrower) stages keep more CTAs per SM

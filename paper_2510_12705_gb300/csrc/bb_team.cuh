@@ -4,7 +4,9 @@
 // apart (Section III-A: two right reflectors act on overlapping column sets,
 // and a left reflector of sweep R+1 reaches the pivot of sweep R's row-bulge
 // two steps ahead), so one CTA runs W consecutive sweeps side by side, one
-// warp ("team") per sweep, and a last warp moves data.
+// team of kTeamWarps warps per sweep (its first warp builds the reflectors,
+// all of them apply them, two threads per row or column, with team barriers),
+// and a last warp moves data.
 //
 // Shared memory holds a circular band window of C columns: matrix column x in
 // slot x mod C, band offsets i - x in [-(2bw-1), bw-1] (the only ones this
@@ -36,7 +38,7 @@ __device__ __forceinline__ bool wait_shared(const int* p, int target, Header* hd
     if (last >= target) { (void)ld_acquire_shared(p); return true; }
     unsigned long long t_last = global_ns();
     for (int it = 1;; ++it) {
-        __nanosleep(40);
+        if (it > 32) __nanosleep(32);
         const int v = ld_relaxed_shared(p);
         if (v >= target) { (void)ld_acquire_shared(p); return true; }
         if ((it & 15) == 0) {
@@ -65,76 +67,94 @@ __host__ __device__ __forceinline__ int team_smem_elems(int bw, int W, int maxm)
     return team_cols(bw, W) * team_pitch(bw) + W * team_scratch_elems(maxm);
 }
 
-// Warp: reflector (v, tau) from the right on window rows [r_lo, r_hi] of the
-// m columns whose slot bases are cb[0..m) (row i of column c+t at
-// cb[t] + i - (c + t)).  One lane per row; the lanes of a pass read
-// consecutive rows of one column; a row's entries are held in registers.
-// Loads go to clamped, always valid addresses (no branch per entry: the
-// loads of a row issue back to back); v is zero beyond m, so the extra terms
-// vanish, and only the stores are guarded.
+// warps per team (one per SM sub-partition)
+constexpr int kTeamWarps = 4;
+
+// Team of nt threads (tt = this thread's index in the team): reflector
+// (v, tau) from the right on window rows [r_lo, r_hi] of the m columns whose
+// slot bases are cb[0..m) (row i of column c+t at cb[t] + i - (c + t)).  Two
+// threads per row: thread p of a pair takes the entries [p H, p H + H) and one
+// shuffle combines the halves.  Loads go to clamped, always valid addresses;
+// v is zero beyond m, so the extra terms vanish, and only the stores are
+// guarded.  Every thread of the team runs the same number of passes.
 template <typename T, int MAXM>
 __device__ __forceinline__ void team_apply_right(T* win, const int* cb, int c, int m, int r_lo,
-                                                 int r_hi, const T* v, T tau)
+                                                 int r_hi, const T* v, T tau, int tt, int nt)
 {
-    const int lane = threadIdx.x & 31;
-    for (int r0 = r_lo; r0 <= r_hi; r0 += 32) {
-        const bool act = r0 + lane <= r_hi;
-        const int r = act ? r0 + lane : r_hi;
-        T a[MAXM];
+    constexpr int H = (MAXM + 1) / 2;
+    const int k0 = (tt & 1) * H, np = nt >> 1;
+    const int nrows = r_hi - r_lo + 1;
+    for (int base = 0; base < nrows; base += np) {
+        const int ri = base + (tt >> 1);
+        const bool act = ri < nrows;
+        const int r = r_lo + (act ? ri : nrows - 1);
+        T a[H];
         T w = (T)0;
 #pragma unroll
-        for (int t = 0; t < MAXM; ++t) {
-            const int tt = t < m ? t : m - 1;
-            a[t] = win[cb[tt] + r - (c + tt)];
-            w = fma(a[t], v[t], w);
+        for (int i = 0; i < H; ++i) {
+            const int t = k0 + i, tc = t < m ? t : m - 1;
+            a[i] = win[cb[tc] + r - (c + tc)];
+            if (t < MAXM) w = fma(a[i], v[t], w);
         }
+        w += __shfl_xor_sync(FULL, w, 1);
         const T tw = tau * w;
         if (act) {
 #pragma unroll
-            for (int t = 0; t < MAXM; ++t)
-                if (t < m) win[cb[t] + r - (c + t)] = fma(-tw, v[t], a[t]);
+            for (int i = 0; i < H; ++i) {
+                const int t = k0 + i;
+                if (t < m) win[cb[t] + r - (c + t)] = fma(-tw, v[t], a[i]);
+            }
         }
     }
 }
 
-// Warp: reflector (v, tau) from the left on rows [c, c+m) of columns
-// [x_lo, x_hi] (column c+k at cb[k]).  One lane per column, its entries in
-// registers; loads as above.
+// Team: reflector (v, tau) from the left on rows [c, c+m) of columns
+// [x_lo, x_hi] (column c+k at cb[k]); two threads per column as above.
 template <typename T, int MAXM>
 __device__ __forceinline__ void team_apply_left(T* win, const int* cb, int c, int m, int x_lo,
-                                                int x_hi, const T* v, T tau)
+                                                int x_hi, const T* v, T tau, int tt, int nt)
 {
-    const int lane = threadIdx.x & 31;
-    for (int x0 = x_lo; x0 <= x_hi; x0 += 32) {
-        const bool act = x0 + lane <= x_hi;
-        const int x = act ? x0 + lane : x_hi;
+    constexpr int H = (MAXM + 1) / 2;
+    const int k0 = (tt & 1) * H, np = nt >> 1;
+    const int ncols = x_hi - x_lo + 1;
+    for (int base = 0; base < ncols; base += np) {
+        const int xi = base + (tt >> 1);
+        const bool act = xi < ncols;
+        const int x = x_lo + (act ? xi : ncols - 1);
         T* col = win + cb[x - c] + (c - x);     // row c + t at col[t]
-        T a[MAXM];
+        T a[H];
         T w = (T)0;
 #pragma unroll
-        for (int t = 0; t < MAXM; ++t) {
-            a[t] = col[t < m ? t : m - 1];
-            w = fma(a[t], v[t], w);
+        for (int i = 0; i < H; ++i) {
+            const int t = k0 + i;
+            a[i] = col[t < m ? t : m - 1];
+            if (t < MAXM) w = fma(a[i], v[t], w);
         }
+        w += __shfl_xor_sync(FULL, w, 1);
         const T tw = tau * w;
         if (act) {
 #pragma unroll
-            for (int t = 0; t < MAXM; ++t)
-                if (t < m) col[t] = fma(-tw, v[t], a[t]);
+            for (int i = 0; i < H; ++i) {
+                const int t = k0 + i;
+                if (t < m) col[t] = fma(-tw, v[t], a[i]);
+            }
         }
     }
 }
 
 template <typename TS, typename T, int MAXM>
-__global__ void __launch_bounds__(544) team_kernel(Launch L)
+__global__ void __launch_bounds__(32 * (4 * kTeamWarps + 1)) team_kernel(Launch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_task[2];
     __shared__ int tprog[16];     // per team: 2 * steps done (+1: right reflector of the next done)
     __shared__ int s_loaded;      // columns < s_loaded are in the window
     __shared__ int s_abort;
+    __shared__ int s_tok[16][2];  // per team: results of its leader's waits (two slots in turn,
+                                  // so a slow reader never sees the next result)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int W = (blockDim.x >> 5) - 1;   // teams; warp W moves data
+    const int W = ((blockDim.x >> 5) - 1) / kTeamWarps;   // teams; warp W * kTeamWarps moves data
+    const int IOW = W * kTeamWarps;
     const int stage = L.stage;
     const int base = stage * PROG_STAGE;
     const int ps = L.prog_stride;
@@ -176,7 +196,7 @@ __global__ void __launch_bounds__(544) team_kernel(Launch L)
         if (tid == 0) { s_loaded = R0 + 1; s_abort = 0; }
         __syncthreads();
 
-        if (warp == W) {
+        if (warp == IOW) {
             // ---------------------------------------------------------- IO warp
             // lane j < kk follows team j: the first column of its next row-bulge
             const int nsj = lane < kk ? sweep_steps(n, bw, d, R0 + lane) : 0;
@@ -249,9 +269,12 @@ __global__ void __launch_bounds__(544) team_kernel(Launch L)
                 if (__shfl_sync(FULL, ab, 0)) { ok = false; break; }
             }
             if (!ok && lane == 0) st_release_shared(&s_abort, 1);
-        } else if (warp < kk) {
+        } else if (warp < IOW && warp / kTeamWarps < kk) {
             // ------------------------------------------------------------- team
-            const int j = warp, R = R0 + j;
+            const int j = warp / kTeamWarps, R = R0 + j;
+            const int tt = tid - j * kTeamWarps * 32, nt = kTeamWarps * 32;
+            const bool lead = (warp % kTeamWarps) == 0;   // builds the reflectors, takes the waits
+            const int bar = 1 + j;                         // named barrier of this team
             const int ns = sweep_steps(n, bw, d, R);
             const int nsp = j > 0 ? sweep_steps(n, bw, d, R - 1) : 0;
             T* const scr = win + C * P + j * team_scratch_elems(MAXM);
@@ -262,54 +285,65 @@ __global__ void __launch_bounds__(544) team_kernel(Launch L)
             T* const ts = xb + MAXM + 1;
             int* const cb = (int*)(ts + 64);    // slot bases of the row-bulge's columns
             bool ok = true;
+            int tk = 0;                         // waits so far: slot tk & 1 of s_tok[j]
             for (int s = 0; s < ns && ok; ++s) {
                 const int c = R + 1 + s * bw;
                 const int m = min(d + 1, n - c);
                 const int r0 = s == 0 ? R : c - bw;
                 const int jmax = min(n - 1, c + m - 1 + bw);
                 // wait: team j-1 completed step s+1 (team 0: the right panel's columns loaded)
-                int w_ok = 1;
-                if (lane == 0) {
-                    w_ok = j > 0 ? (int)wait_shared(&tprog[j - 1], 2 * min(s + 2, nsp), L.hdr, L.timeout_ns)
-                                 : (int)wait_shared(&s_loaded, c + m, L.hdr, L.timeout_ns);
-                }
-                if (!__shfl_sync(FULL, w_ok, 0)) { ok = false; break; }
-                for (int k = lane; k <= jmax - c; k += 32) cb[k] = ((c + k) % C) * P + 2 * bw - 1;
-                __syncwarp();
+                if (lead && lane == 0)
+                    s_tok[j][tk & 1] = j > 0 ? (int)wait_shared(&tprog[j - 1], 2 * min(s + 2, nsp), L.hdr, L.timeout_ns)
+                                     : (int)wait_shared(&s_loaded, c + m, L.hdr, L.timeout_ns);
+                for (int k = tt; k <= jmax - c; k += nt) cb[k] = ((c + k) % C) * P + 2 * bw - 1;
+                bar_sync_n(bar, nt);
+                if (!s_tok[j][tk++ & 1]) { ok = false; break; }
                 // right reflector from row r0, columns c .. c+m-1
-                for (int t = lane; t < m; t += 32) xb[t] = win[cb[t] + r0 - (c + t)];
-                __syncwarp();
-                fast_reflector<T, MAXM>(m, xb, vR, tb);
-                __syncwarp();
-                for (int t = lane; t < m; t += 32) win[cb[t] + r0 - (c + t)] = t == 0 ? tb[1] : (T)0;
-                team_apply_right<T, MAXM>(win, cb, c, m, r0 + 1, c + m - 1, vR, tb[0]);
-                __syncwarp();
-                if (lane == 0) st_release_shared(&tprog[j], 2 * s + 1);
-                // left reflector from column c, rows c .. c+m-1
-                fast_reflector<T, MAXM>(m, win + cb[0], vL, tb + 4);
-                __syncwarp();
-                for (int t = lane; t < m; t += 32) win[cb[0] + t] = t == 0 ? tb[5] : (T)0;
-                // the last column c + d + bw is shared with team j-1's row-bulge s+2
-                const int xt = c + d + bw;
-                const bool tail = xt <= jmax;
-                if (lane == 0) {
-                    if (j == 0) w_ok = (int)wait_shared(&s_loaded, jmax + 1, L.hdr, L.timeout_ns);
-                    else if (tail)
-                        w_ok = (int)wait_shared(&tprog[j - 1], s + 2 < nsp ? 2 * (s + 2) + 1 : 2 * nsp,
-                                                L.hdr, L.timeout_ns);
+                if (lead) {
+                    for (int t = lane; t < m; t += 32) xb[t] = win[cb[t] + r0 - (c + t)];
+                    __syncwarp();
+                    fast_reflector<T, MAXM>(m, xb, vR, tb);
+                    __syncwarp();
+                    for (int t = lane; t < m; t += 32) win[cb[t] + r0 - (c + t)] = t == 0 ? tb[1] : (T)0;
                 }
-                if (!__shfl_sync(FULL, w_ok, 0)) { ok = false; break; }
-                team_apply_left<T, MAXM>(win, cb, c, m, c + 1, jmax, vL, tb[4]);
-                __syncwarp();
+                bar_sync_n(bar, nt);
+                team_apply_right<T, MAXM>(win, cb, c, m, r0 + 1, c + m - 1, vR, tb[0], tt, nt);
+                bar_sync_n(bar, nt);
+                if (lead && lane == 0) st_release_shared(&tprog[j], 2 * s + 1);
+                // left reflector from column c, rows c .. c+m-1
+                if (lead) {
+                    fast_reflector<T, MAXM>(m, win + cb[0], vL, tb + 4);
+                    __syncwarp();
+                    for (int t = lane; t < m; t += 32) win[cb[0] + t] = t == 0 ? tb[5] : (T)0;
+                    // the last column c + d + bw is shared with team j-1's row-bulge s+2
+                    const int xt = c + d + bw;
+                    const bool tail = xt <= jmax;
+                    if (lane == 0) {
+                        int w_ok = 1;
+                        if (j == 0) w_ok = (int)wait_shared(&s_loaded, jmax + 1, L.hdr, L.timeout_ns);
+                        else if (tail)
+                            w_ok = (int)wait_shared(&tprog[j - 1], s + 2 < nsp ? 2 * (s + 2) + 1 : 2 * nsp,
+                                                    L.hdr, L.timeout_ns);
+                        s_tok[j][tk & 1] = w_ok;
+                    }
+                }
+                bar_sync_n(bar, nt);
+                if (!s_tok[j][tk++ & 1]) { ok = false; break; }
+                team_apply_left<T, MAXM>(win, cb, c, m, c + 1, jmax, vL, tb[4], tt, nt);
+                bar_sync_n(bar, nt);
                 // a sweep can be one row-bulge shorter than its predecessor: its
                 // completion is published once the predecessor is complete, so
                 // a completed sweep vouches for the whole chain before it
-                if (lane == 0 && s == ns - 1 && j > 0)
-                    w_ok = (int)wait_shared(&tprog[j - 1], 2 * nsp, L.hdr, L.timeout_ns);
-                if (!__shfl_sync(FULL, w_ok, 0)) { ok = false; break; }
-                if (lane == 0) st_release_shared(&tprog[j], 2 * (s + 1));
+                if (lead && lane == 0) {
+                    int w_ok = 1;
+                    if (s == ns - 1 && j > 0) w_ok = (int)wait_shared(&tprog[j - 1], 2 * nsp, L.hdr, L.timeout_ns);
+                    if (w_ok) st_release_shared(&tprog[j], 2 * (s + 1));
+                    s_tok[j][tk & 1] = w_ok;
+                }
+                bar_sync_n(bar, nt);
+                if (!s_tok[j][tk++ & 1]) { ok = false; break; }
             }
-            if (!ok && lane == 0) st_release_shared(&s_abort, 1);
+            if (!ok && lead && lane == 0) st_release_shared(&s_abort, 1);
         }
         __syncthreads();
         if (s_abort || ld_relaxed(&L.hdr->abort)) break;

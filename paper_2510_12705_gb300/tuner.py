@@ -1,7 +1,9 @@
 """Hyperparameter tuning for the band -> bidiagonal reduction.
 
-The kernel's three knobs (Section III-C): the inner tilewidth TW, the threads
-per bulge (CTA size) and the number of sweeps processed concurrently.
+The knobs (Section III-C): the inner tilewidth TW, the number of sweeps
+processed concurrently ("max blocks": CTAs per SM) and, for the group kernel,
+the number of sweeps one CTA chases together (the max-blocks unrolled into one
+block).  The CTA size follows the panel size.
 
 * Exhaustive autotuner: ``autotune(n, b, dtype)`` times every candidate on a
   synthetic band of that size through the native ``bb_autotune`` (Section IV
@@ -30,29 +32,29 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-TWS = (16, 32)             # TW = 8 (also in the paper's search) never won on GB300
-TPBS = (0, 256)            # 0: sized per stage (two threads per panel row + a reflector warp)
-SIFS = (0, 1)              # 0: as many resident sweeps as fit; 1: one per SM
+TWS = (16, 24, 32)         # TW = 8 (also in the paper's search) never won on GB300
+GROUPS = (8, 24)           # sweeps per CTA of the group kernel (at most; fewer where 3K + d > bw)
+SIFS = (0, 1)              # 0: the library's choice of resident CTAs; 1: one CTA per SM on every stage
 IN_DIM = 8
 HIDDEN = 32
 
 
 def candidates():
-    return [(tw, tpb, sif) for tw in TWS for tpb in TPBS for sif in SIFS]
+    return [(tw, g, sif) for tw in TWS for g in GROUPS for sif in SIFS]
 
 
 def features(n: int, b: int, dtype: str, cand) -> list[float]:
-    tw, tpb, sif = cand
+    tw, g, sif = cand
     ln, lb = math.log2(max(n, 2)), math.log2(max(b, 1))
     return [(ln - 13.0) / 3.0, (lb - 6.0) / 2.0, 1.0 if dtype == "f64" else -1.0,
-            (math.log2(tw) - 4.0), 1.0 if tpb else -1.0, 1.0 if sif else -1.0,
+            (math.log2(tw) - 4.5), (math.log2(g) - 4.0), 1.0 if sif else -1.0,
             (ln - lb - 7.0) / 3.0, (lb - math.log2(tw) - 2.0) / 2.0]
 
 
 def _tuning(cand, nsm: int):
     import paper_2510_12705_gb300 as bb
-    tw, tpb, sif = cand
-    return bb.Tuning(tw=tw, tpb=tpb, sweeps_in_flight=(nsm if sif else 0))
+    tw, g, sif = cand
+    return bb.Tuning(tw=tw, group=g, sweeps_in_flight=(nsm if sif else 0))
 
 
 def usable(n: int, b: int, dtype: str, cand) -> bool:
@@ -103,23 +105,22 @@ def collect(grid, reps: int = 1, log=None, out=None):
 
 
 HELD_OUT = (65536, 256, "f32")
+DEFAULT_GROUP = 24         # the library's default sweeps per CTA (group = 0)
 
 
-def default_grid(n_max: int = 65536, max_nb: int = 1 << 23):
-    """Training grid: n = 1024, 2048, ... n_max; b in {16, 32, ..., 512} with
-    b <= n/4 and n*b <= max_nb (the cost of one reduction grows like n*b),
-    plus n = 65536, b = 256 in FP64; FP32 and FP64.  The held-out problem
-    n = 65536, b = 256, FP32 is never part of it."""
+def default_grid(n_max: int = 32768, max_nb: int = 1 << 22):
+    """Training grid: n = 1024, 2048, ... n_max; b in {16, 32, ..., 256} with
+    b <= n/4 and n*b <= max_nb (the cost of one reduction grows like n*b);
+    FP32 and FP64.  The held-out problem n = 65536, b = 256, FP32 is never
+    part of it (it lies outside the grid)."""
     grid = []
     n = 1024
     while n <= n_max:
-        for b in (16, 32, 64, 128, 256, 512):
+        for b in (16, 32, 64, 128, 256):
             if b <= n // 4 and n * b <= max_nb:
                 for dtype in ("f32", "f64"):
                     grid.append((n, b, dtype))
         n *= 2
-    if n_max >= 65536:
-        grid.append((65536, 256, "f64"))
     return [g for g in grid if g != HELD_OUT]
 
 
@@ -198,7 +199,7 @@ class MlpTuner:
         return [math.exp(float(y) + self.mean) for y in self.forward(X).cpu().numpy()]
 
     def predict(self, n, b, dtype):
-        """Candidate (tw, tpb, sif) with the smallest predicted time among those
+        """Candidate (tw, group, sif) with the smallest predicted time among those
         the problem can use on this device."""
         t = self.predict_ms(n, b, dtype)
         ok = [i for i, c in enumerate(candidates()) if usable(n, b, dtype, c)]
@@ -231,7 +232,7 @@ def evaluate(tuner: "MlpTuner", n: int, b: int, dtype: str, reps: int = 1) -> di
     pick = tuple(tuner.predict(n, b, dtype))
     times, best = autotune(n, b, dtype, reps=reps)
     dflt = bb.bb_default_tuning(n, b, bb.BB_F64 if dtype == "f64" else bb.BB_F32)
-    dflt_c = (dflt.tw, 0, 0)
+    dflt_c = (dflt.tw, DEFAULT_GROUP, 0)
     out = {"n": n, "b": b, "dtype": dtype,
            "exhaustive_best": list(cands[best]), "exhaustive_ms": times[best],
            "mlp_pick": list(pick), "mlp_ms": times[cands.index(pick)],
@@ -259,9 +260,9 @@ def tuning_for(n: int, b: int, dtype: str, device: int = 0):
     t = bb.bb_default_tuning(n, b, code)
     if not os.path.exists(MODEL_PATH):
         return t, "library default"
-    tw, tpb, sif = MlpTuner.load(MODEL_PATH).predict(n, b, dtype)
+    tw, g, sif = MlpTuner.load(MODEL_PATH).predict(n, b, dtype)
     nsm = torch.cuda.get_device_properties(device).multi_processor_count
-    return bb.Tuning(tw=tw, tpb=tpb, sweeps_in_flight=nsm if sif else 0,
+    return bb.Tuning(tw=tw, group=g, sweeps_in_flight=nsm if sif else 0,
                      timeout_s=t.timeout_s), "learned tuner"
 
 
@@ -271,7 +272,7 @@ def main(argv=None):
     c = sub.add_parser("collect")
     c.add_argument("--out", required=True)
     c.add_argument("--reps", type=int, default=1)
-    c.add_argument("--n-max", type=int, default=65536)
+    c.add_argument("--n-max", type=int, default=32768)
     t = sub.add_parser("train")
     t.add_argument("--data", required=True)
     t.add_argument("--out", required=True)

@@ -206,13 +206,13 @@ def test_shared_bytes_model(bb):
 def test_tuner_features_and_grid():
     from paper_2510_12705_gb300 import tuner
     c = tuner.candidates()
-    assert len(c) == len(set(c)) == len(tuner.TWS) * len(tuner.TPBS) * len(tuner.SIFS)
+    assert len(c) == len(set(c)) == len(tuner.TWS) * len(tuner.GROUPS) * len(tuner.SIFS)
     f = tuner.features(65536, 256, "f32", c[0])
     assert len(f) == tuner.IN_DIM and all(abs(x) < 4 for x in f)
     g = tuner.default_grid()
-    assert all(b <= n // 4 and (n * b <= (1 << 23) or (n, b) == (65536, 256)) for n, b, _ in g)
-    assert (65536, 256, "f32") not in g and (65536, 256, "f64") in g
-    assert len(set(g)) == len(g)
+    assert all(b <= n // 4 and n * b <= (1 << 22) for n, b, _ in g)
+    assert (65536, 256, "f32") not in g
+    assert {dt for _, _, dt in g} == {"f32", "f64"} and len(set(g)) == len(g)
 
 
 def test_workspace_size_model(bb):
