@@ -144,3 +144,29 @@ def test_one_call_batched_equals_plan():
     for (_, _, d1, e1, _), (_, _, d2, e2, _) in zip(a, b_):
         n = d1.numel()
         assert torch.equal(d1, d2) and torch.equal(e1[: n - 1], e2[: n - 1])
+
+
+def test_cfg4_sample_sigma_vs_oracle():
+    """The 512-matrix batch of the batched workload (n ~ U[256, 4096],
+    b in {8, 16, 32, 64}, FP32, seed 3), reduced in one plan: the four
+    largest matrices and four others of the batch against the FP64 oracle's
+    singular values at the FP32 tolerance."""
+    import torch
+    import paper_2510_12705_gb300 as bb
+    probs = bandgen.batch_problems(512, seed=3)
+    items = _make(probs, torch.float32)
+    plan = bb.BatchPlan([(band, b, d, e) for band, b, d, e, _ in items])
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.execute(ws)
+    torch.cuda.synchronize()
+    assert bb.bb_device_status(reset=True) == 0
+    order = sorted(range(len(probs)), key=lambda i: -probs[i][0])
+    sample = order[:4] + [order[len(order) // 4], order[len(order) // 2], order[-2], order[-1]]
+    assert max(probs[i][0] for i in sample) > 3500
+    for i in sample:
+        band, b, d, e, ab = items[i]
+        n = band.shape[0]
+        d0, e0, _ = oracle.band_to_bidiag(ab, b, 32)
+        s0 = oracle.bidiag_sigma(d0, e0)
+        s = oracle.bidiag_sigma(d.cpu().numpy().astype(np.float64), e[: n - 1].cpu().numpy().astype(np.float64))
+        assert np.max(np.abs(s - s0)) <= TOL_F32 * s0[0], (n, b)
