@@ -141,6 +141,31 @@ def _haar_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
     return q * np.sign(np.diag(r))
 
 
+def prescribed_sigma_dense(n: int, profile: str, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Dense n x n matrix A = U diag(sigma) V^T with Haar-random orthogonal U, V
+    and prescribed singular values (the paper's accuracy-experiment input,
+    Section V-A).  ``profile``: "arithmetic" (uniform spacing in (0, 1]),
+    "logarithmic" (1 .. 1e-8, geometric) or "quartercircle" (quantiles of the
+    quarter-circle law on [0, 1]).  Returns (A as a C-ordered array, sigma
+    sorted descending)."""
+    rng = _rng(seed)
+    if profile == "arithmetic":
+        sigma = np.arange(n, 0, -1) / n
+    elif profile == "logarithmic":
+        sigma = np.logspace(0.0, -8.0, n)
+    elif profile == "quartercircle":
+        # inverse CDF of the quarter circle density (4/pi) sqrt(1 - x^2) on [0, 1]
+        p = (np.arange(n) + 0.5) / n
+        xs = np.linspace(0.0, 1.0, 20001)
+        cdf = (2.0 / np.pi) * (xs * np.sqrt(1.0 - xs * xs) + np.arcsin(xs))
+        sigma = np.sort(np.interp(p, cdf, xs))[::-1]
+    else:
+        raise ValueError(profile)
+    u = _haar_orthogonal(n, rng)
+    v = _haar_orthogonal(n, rng)
+    return (u * sigma) @ v.T, sigma
+
+
 def prescribed_sigma_band(n: int, b: int, profile: str, seed: int,
                           ldab: int | None = None) -> tuple[np.ndarray, np.ndarray]:
     """Band matrix with prescribed singular values (accuracy experiment input).
@@ -157,22 +182,7 @@ def prescribed_sigma_band(n: int, b: int, profile: str, seed: int,
     (1 .. 1e-8, geometric), or "quartercircle" (quantiles of the quarter-circle
     law on [0, 1]).  Returns (ab of shape (n, ldab), sigma sorted descending).
     """
-    rng = _rng(seed)
-    if profile == "arithmetic":
-        sigma = np.arange(n, 0, -1) / n
-    elif profile == "logarithmic":
-        sigma = np.logspace(0.0, -8.0, n)
-    elif profile == "quartercircle":
-        # inverse CDF of the quarter circle density (4/pi) sqrt(1 - x^2) on [0, 1]
-        p = (np.arange(n) + 0.5) / n
-        xs = np.linspace(0.0, 1.0, 20001)
-        cdf = (2.0 / np.pi) * (xs * np.sqrt(1.0 - xs * xs) + np.arcsin(xs))
-        sigma = np.sort(np.interp(p, cdf, xs))[::-1]
-    else:
-        raise ValueError(profile)
-    u = _haar_orthogonal(n, rng)
-    v = _haar_orthogonal(n, rng)
-    a = (u * sigma) @ v.T
+    a, sigma = prescribed_sigma_dense(n, profile, seed)
     # dense -> band: for each panel k, annihilate below the diagonal block
     # (left QR) and beyond the band (right QR of the transposed row block).
     for k in range(0, n, b):

@@ -284,6 +284,32 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
                 float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * Stage 1 of the SVD (Section II: the dense matrix is reduced to band form
+ * first; Section V-A: the accuracy experiments start from dense matrices):
+ * dense_to_band -- the dense n x n matrix `a` (device, column-major,
+ * leading dimension lda >= n, `dtype` BB_F64 or BB_F32; read, never written)
+ * to upper band form B = Q^T A P with bandwidth b, written to band_out
+ * (device, the LAPACK 'U' layout of band_to_bidiag's input:
+ * B[i][j] at band_out[(b + i - j) + j * ldab], ldab >= b + 1; slots above row
+ * 0 are set to zero), so its output can be passed to band_to_bidiag as is.
+ * Method: Householder QR of b-wide column panels and LQ of b-wide row panels
+ * (the larfg convention of the reduction above), the panels by this library's
+ * kernels, the compact-WY trailing updates by cuBLAS GEMMs in `dtype`; b >= n-1
+ * gives the R of a Householder QR.  The singular values of B are those of A
+ * up to rounding.  workspace: device, >= dense_to_band_workspace_size(n, b,
+ * dtype) bytes (a working copy of A plus O(n b)), 256-byte aligned; NULL =
+ * allocate it from the stream-ordered allocator.  Calls on one device
+ * serialise on the library's cuBLAS handle for that device.  Asynchronous on
+ * `stream`.  Returns BB_OK, BB_ERR_ARG (n < 1, b < 1, lda < n, ldab < b + 1,
+ * NULL pointers, bad dtype), BB_ERR_UNSUPPORTED (16-bit dtypes, n > 2^30),
+ * BB_ERR_WORKSPACE, BB_ERR_ALLOC or BB_ERR_LAUNCH.  The workspace-size query
+ * returns 0 for invalid arguments.
+ */
+size_t dense_to_band_workspace_size(int64_t n, int64_t b, int dtype);
+int dense_to_band(int64_t n, int64_t b, int dtype, const void *a, int64_t lda, void *band_out,
+                  int64_t ldab, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Singular values of the upper bidiagonal produced above (the third SVD
  * stage, which the paper hands to LAPACK: Sections V-A and VII), on the GPU.
  * bb_bidiag_sigma -- sigma_out[0..n-1] (device, FP64, descending) = the

@@ -101,6 +101,8 @@ def lib():
             "bb_autotune": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, ci, ci,
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci), vp]),
             "bb_bidiag_sigma_workspace_size": (sz, [i64]),
+            "dense_to_band_workspace_size": (sz, [i64, i64, ci]),
+            "dense_to_band": (ci, [i64, i64, ci, vp, i64, vp, i64, vp, sz, vp]),
             "bb_bidiag_sigma": (ci, [i64, ci, vp, vp, vp, vp, sz, vp]),
             "bb_mlp_param_count": (sz, [ci, ci]),
             "bb_mlp_backward_scratch": (sz, [ci, ci]),
@@ -275,6 +277,32 @@ def bb_measure_l2_bandwidth(nbytes: int = 32 << 20, reps: int = 200, stream=None
 
 def bb_measure_fma_peak(dtype: int, stream=None) -> float:
     return float(lib().bb_measure_fma_peak(dtype, _stream_handle(stream)))
+
+
+def dense_to_band(a, b: int, band_out, workspace=None, stream=None) -> None:
+    """Stage 1 (dense_to_band): the dense CUDA matrix ``a`` (n x n, float32 or
+    float64; read, never written) to upper band form with bandwidth b, written
+    to ``band_out`` in the layout band_to_bidiag takes (a CUDA tensor (n, ldab),
+    ldab >= b + 1, row j holding column j of the band).  ``a`` is seen
+    column-major: a row-major tensor passes its transpose, which has the same
+    singular values (use ``a.t().contiguous()`` for A itself)."""
+    n = a.shape[0]
+    if a.dim() != 2 or a.shape[1] != n or not a.is_cuda or not a.is_contiguous():
+        raise ValueError("a must be a contiguous square CUDA tensor")
+    if not band_out.is_cuda or band_out.dim() != 2 or band_out.shape[0] != n or band_out.dtype != a.dtype \
+            or not band_out.is_contiguous():
+        raise ValueError("band_out must be a contiguous CUDA tensor (n, ldab) of a's dtype")
+    code = _dtype_code(a.dtype)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    rc = lib().dense_to_band(n, b, code, a.data_ptr(), n, band_out.data_ptr(), band_out.shape[1],
+                             ws_ptr, ws_bytes, _stream_handle(stream))
+    _check(rc, "dense_to_band")
+
+
+def dense_to_band_workspace_size(n: int, b: int, dtype: int) -> int:
+    return int(lib().dense_to_band_workspace_size(n, b, dtype))
 
 
 class BatchPlan:

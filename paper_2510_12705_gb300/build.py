@@ -60,7 +60,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = OUT + f".{os.getpid()}.tmp"
-    cmd = [cc, *ARCH, "-shared", "--cudart=static", "-o", tmp, *objs]
+    # cuBLAS: the plain GEMMs of the dense -> band stage (bb_dense.cu)
+    cmd = [cc, *ARCH, "-shared", "--cudart=static", "-o", tmp, *objs, "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

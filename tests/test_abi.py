@@ -260,3 +260,24 @@ def test_stage_counts_sum_to_schedule(bb, n, b, tw):
     assert sum(p.steps for p in parts) == tot.steps
     assert sum(p.flops for p in parts) == pytest.approx(tot.flops, rel=1e-12)
     assert sum(p.elements for p in parts) == pytest.approx(tot.elements, rel=1e-12)
+
+
+def test_dense_to_band_argument_checks(bb):
+    """dense_to_band rejects bad arguments before any GPU work (Section V-A's
+    stage 1 entry point)."""
+    L = bb.lib()
+    fake = 0x1000
+    n, b = 64, 8
+    assert L.dense_to_band(0, b, bb.BB_F64, fake, 64, fake, 9, None, 0, None) == bb.BB_ERR_ARG
+    assert L.dense_to_band(n, 0, bb.BB_F64, fake, 64, fake, 9, None, 0, None) == bb.BB_ERR_ARG
+    assert L.dense_to_band(n, b, bb.BB_F64, fake, 63, fake, 9, None, 0, None) == bb.BB_ERR_ARG
+    assert L.dense_to_band(n, b, bb.BB_F64, fake, 64, fake, 8, None, 0, None) == bb.BB_ERR_ARG
+    assert L.dense_to_band(n, b, bb.BB_F64, None, 64, fake, 9, None, 0, None) == bb.BB_ERR_ARG
+    assert L.dense_to_band(n, b, bb.BB_F16, fake, 64, fake, 9, None, 0, None) == bb.BB_ERR_UNSUPPORTED
+    assert L.dense_to_band(n, b, 9, fake, 64, fake, 9, None, 0, None) == bb.BB_ERR_ARG
+    assert L.dense_to_band(n, b, bb.BB_F64, fake, 64, fake, 9, fake, 16, None) == bb.BB_ERR_WORKSPACE
+    assert bb.dense_to_band_workspace_size(0, b, bb.BB_F64) == 0
+    assert bb.dense_to_band_workspace_size(n, b, bb.BB_F16) == 0
+    ws64 = bb.dense_to_band_workspace_size(n, b, bb.BB_F64)
+    assert 8 * n * n <= ws64 <= 8 * n * n + 8 * (6 * n * b + 2 * b * b) + 4096
+    assert bb.dense_to_band_workspace_size(n, b, bb.BB_F32) < ws64
