@@ -284,6 +284,31 @@ int bb_mlp_adam(int count, float *params, const float *grads, float *m, float *v
                 float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * Singular vectors of the band stage (Section VII: the back-transformation of
+ * the stored reflectors): band_to_bidiag_vectors -- the reduction of
+ * band_to_bidiag (same arguments and outputs d_out, e_out), which also stores
+ * every Householder reflector it builds, followed by the back-transformation
+ * that forms the orthogonal Q (q_out) and P (p_out), n x n, column-major
+ * (device, leading dimensions ldq, ldp >= n, `dtype`), with
+ * Q^T A P = B = bidiag(d, e); Q and P have e1 as their first column and row.
+ * The singular vectors of A are then Q and P times those of B.  The last
+ * stage always runs one sweep per CTA here (teams are ignored).  workspace:
+ * device, >= band_to_bidiag_vectors_workspace_size(n, b, dtype, tuning)
+ * bytes, 256-byte aligned (the reduction's workspace plus two slots of
+ * (MAXM + 1) values, rounded up to 4, per row-bulge); NULL = allocate it from
+ * the stream-ordered allocator.  Cost: the reduction plus two passes over the
+ * reflectors, one thread per row of Q and P.  Asynchronous on `stream`.
+ * Returns the codes of band_to_bidiag_ex, BB_ERR_ARG also for NULL q_out /
+ * p_out or ldq, ldp < n, and BB_ERR_UNSUPPORTED for 16-bit dtypes.  The
+ * workspace-size query returns 0 for invalid arguments.
+ */
+size_t band_to_bidiag_vectors_workspace_size(int64_t n, int64_t b, int dtype, const bb_tuning *tuning);
+int band_to_bidiag_vectors(int64_t n, int64_t b, int dtype, const void *band, int64_t ldab,
+                           void *d_out, void *e_out, void *q_out, int64_t ldq, void *p_out,
+                           int64_t ldp, const bb_tuning *tuning, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
+/*
  * Stage 1 of the SVD (Section II: the dense matrix is reduced to band form
  * first; Section V-A: the accuracy experiments start from dense matrices):
  * dense_to_band -- the dense n x n matrix `a` (device, column-major,

@@ -102,6 +102,8 @@ def lib():
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci), vp]),
             "bb_bidiag_sigma_workspace_size": (sz, [i64]),
             "dense_to_band_workspace_size": (sz, [i64, i64, ci]),
+            "band_to_bidiag_vectors_workspace_size": (sz, [i64, i64, ci, tp]),
+            "band_to_bidiag_vectors": (ci, [i64, i64, ci, vp, i64, vp, vp, vp, i64, vp, i64, tp, vp, sz, vp]),
             "dense_to_band": (ci, [i64, i64, ci, vp, i64, vp, i64, vp, sz, vp]),
             "bb_bidiag_sigma": (ci, [i64, ci, vp, vp, vp, vp, sz, vp]),
             "bb_mlp_param_count": (sz, [ci, ci]),
@@ -299,6 +301,25 @@ def dense_to_band(a, b: int, band_out, workspace=None, stream=None) -> None:
     rc = lib().dense_to_band(n, b, code, a.data_ptr(), n, band_out.data_ptr(), band_out.shape[1],
                              ws_ptr, ws_bytes, _stream_handle(stream))
     _check(rc, "dense_to_band")
+
+
+def band_to_bidiag_vectors(band, b: int, d_out, e_out, q_out, p_out, tuning=None, workspace=None,
+                           stream=None) -> None:
+    """band_to_bidiag plus the orthogonal factors: Q (q_out) and P (p_out), CUDA
+    tensors (n, n) of the band's dtype holding the column-major factors, so
+    that Q^T A P = bidiag(d, e); as row-major tensors they read as Q^T and P^T."""
+    n, ldab = _check_band(band, d_out, e_out)
+    for x in (q_out, p_out):
+        if not x.is_cuda or x.dtype != band.dtype or x.shape != (n, n) or not x.is_contiguous():
+            raise ValueError("q_out and p_out must be contiguous (n, n) CUDA tensors of the band's dtype")
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    rc = lib().band_to_bidiag_vectors(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab, d_out.data_ptr(),
+                                      e_out.data_ptr() if n > 1 else None, q_out.data_ptr(), n,
+                                      p_out.data_ptr(), n, _tuning_ptr(tuning), ws_ptr, ws_bytes,
+                                      _stream_handle(stream))
+    _check(rc, "band_to_bidiag_vectors")
 
 
 def dense_to_band_workspace_size(n: int, b: int, dtype: int) -> int:

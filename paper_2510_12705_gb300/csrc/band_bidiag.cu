@@ -144,7 +144,7 @@ __device__ __forceinline__ void left_store(const T* LP, TS* __restrict__ W, int 
 // row-bulge publishes its own right half (half_prog = half_value) after C.
 // Returns false when a wait gave up.
 template <typename TS, typename T, int MAXM>
-__device__ __forceinline__ bool row_bulge(const Desc& D, TS* __restrict__ W, int bw, int d, int R,
+__device__ __forceinline__ bool row_bulge(const Launch& L, const Desc& D, TS* __restrict__ W, int bw, int d, int R,
                                           int s, T* RP, T* LP, T* wbuf, T* tsR, T* tsL, T* vR, T* vL,
                                           T* tb, int* s_flag, const int* tail_prog, int tail_target,
                                           int tail_start, Header* hdr, unsigned long long timeout_ns,
@@ -193,6 +193,10 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, TS* __restrict__ W, int
             const ReflScale sc = reflector_scale<T>(m, RP, tsR);
             bar_arrive(1, nt);
             reflector_finish<T>(m, sc, vR, tb);
+            if (L.refl) {
+                __syncwarp();
+                warp_store_reflector<T, MAXM>(L, n, bw, d, R, s, 0, m, vR, tb[0]);
+            }
         }
     } else {
         if (!carried) bar_sync_n(1, nt);
@@ -236,6 +240,10 @@ __device__ __forceinline__ bool row_bulge(const Desc& D, TS* __restrict__ W, int
         const ReflScale sc = reflector_scale<T>(m, LP, tsL);
         bar_arrive(1, d_count);
         reflector_finish<T>(m, sc, vL, tbL);
+        if (L.refl) {
+            __syncwarp();
+            warp_store_reflector<T, MAXM>(L, n, bw, d, R, s, 1, m, vL, tbL[0]);
+        }
     } else {
         const T tau = tb[0], vs = tb[2];
         for (int ri = ri_c + pi; ri < nr; ri += np) {             // C1 -> LP
@@ -427,6 +435,10 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
             if (carried && tid < 32) {
                 const int cs = R + (bw - d) + s * bw;
                 warp_reflector<T>(min(d + 1, n - cs), RP, tsR, vR, tb);
+                if (L.refl) {
+                    __syncwarp();
+                    warp_store_reflector<T, MAXM>(L, n, bw, d, R, s, 0, min(d + 1, n - cs), vR, tb[0]);
+                }
             }
             if (tid == (carried ? 32 : 0)) {
                 bool w_ok = true;
@@ -439,7 +451,7 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
             if (!s_ok) { ok = false; break; }
             const bool carry_out = s + 1 < ns;
             const bool step_ok = row_bulge<TS, T, MAXM>(
-                D, W, bw, d, R, s, RP, LP, wbuf, tsR, tsL, vR, vL, tb, &s_tail_ok,
+                L, D, W, bw, d, R, s, RP, LP, wbuf, tsR, tsL, vR, vL, tb, &s_tail_ok,
                 R > 0 ? &prog[(R - 1) * ps] : nullptr,
                 base + (s + tail_ahead < nsp ? 2 * (s + tail_ahead) + tail_half : 2 * nsp),
                 tail_start, L.hdr, L.timeout_ns,
@@ -467,6 +479,65 @@ __global__ void __launch_bounds__(512) bulge_kernel(Launch L)
         }
         if (!ok) break;
         if (tid == 0 && !stall && ns == 0) st_release(&prog[R * ps], base);
+    }
+}
+
+// ---------------------------------------------------- back-transformation
+// The orthogonal factors of B = Q^T A P from the reflectors the reduction
+// stored (Section VII names the back-transformation of the stored reflectors
+// as the step that turns the method into a singular-vector solver).  In the
+// sequential order of the reduction (stage, sweep, row-bulge), Q = H_L1 H_L2 ...
+// and P = H_R1 H_R2 ..., each H = I - tau v v^T acting on the m = min(d+1, n-c)
+// columns c .. c+m-1 of its row-bulge (c = R + bw' + s bw).  X <- X H touches
+// every row of X independently, so each thread owns one row of X, starts from
+// the identity and applies every reflector of its side in that order.  The
+// GPU's own order of the reflectors differs from the sequential one only in
+// pairs that act on opposite sides (Section III-A schedule), which the product
+// of one side does not see.
+template <typename T>
+__global__ void identity_kernel(T* __restrict__ X, int64_t ldx, int n)
+{
+    const int64_t total = (int64_t)n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n), i = (int)(t % n);
+        X[i + (int64_t)j * ldx] = (T)(i == j ? 1 : 0);
+    }
+}
+
+template <typename T, int MAXM>
+__global__ void backtransform_kernel(int n, int b, int tw, int side, const T* __restrict__ refl,
+                                     T* __restrict__ X, int64_t ldx)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    T* row = X + r;
+    int64_t k = 0;
+    for (int bw = b; bw > 1;) {
+        const int d = min(tw, bw - 1);
+        for (int R = 0; R < n - 1; ++R) {
+            const int ns = sweep_steps(n, bw, d, R);
+            for (int s = 0; s < ns; ++s, ++k) {
+                const int c = R + (bw - d) + s * bw;
+                const int m = min(d + 1, n - c);
+                const T* slot = refl + (2 * k + side) * (int64_t)refl_stride(MAXM);
+                const T tau = __ldg(slot + MAXM);
+                if (tau == (T)0) continue;
+                T x[MAXM];
+                T w = (T)0;
+#pragma unroll
+                for (int t = 0; t < MAXM; ++t) {
+                    if (t < m) {
+                        x[t] = row[(int64_t)(c + t) * ldx];
+                        w = fma(x[t], __ldg(slot + t), w);
+                    }
+                }
+                const T f = tau * w;
+#pragma unroll
+                for (int t = 0; t < MAXM; ++t)
+                    if (t < m) row[(int64_t)(c + t) * ldx] = fma(-f, __ldg(slot + t), x[t]);
+            }
+        }
+        bw -= d;
     }
 }
 
@@ -741,7 +812,14 @@ int launch_stages(const LaunchPlan& P, cudaStream_t st)
     if (!P.tsmem) L.team = 0;
     bool first = true;
     int nlaunch = 0;
+    int64_t refl_base = 0;    // row-bulges of the earlier stages (reflector store of one problem)
     for (int stage = 0; stage < P.max_stages; ++stage) {
+        L.refl_base = refl_base;
+        if (L.refl && stage < P.descs[0].nstages) {
+            const Desc& D0 = P.descs[0];
+            const int bw0 = D0.b - stage * L.tw, d0 = std::min(L.tw, bw0 - 1);
+            refl_base += steps_before(D0.n, bw0, d0, D0.n);
+        }
         // widest stage bandwidth over the problems of each kernel, and the
         // tasks (problems x groups) of the group and team kernels
         int bw_max = 0, d_max = 0, gbw_max = 0, gd_max = 0;
@@ -945,6 +1023,110 @@ int band_to_bidiag_ex(int64_t n, int64_t b, int dtype, const void* band, int64_t
         own = true;
     }
     rc = enqueue(&P, ws, nullptr, st);
+    if (own) cudaFreeAsync(ws, st);
+    return rc;
+}
+
+// ---- singular vectors: reflector store and back-transformation
+
+}  // extern "C"
+
+namespace {
+
+// the tuning of the vectors path: as given, with the last stage on the
+// per-sweep kernel (the team kernel does not store reflectors)
+bb_tuning vectors_tuning(int64_t n, int64_t b, int dtype, const bb_tuning* t)
+{
+    bb_tuning v;
+    if (t) v = *t;
+    else bb_default_tuning(n, b, dtype, &v);
+    v.teams = -1;
+    return v;
+}
+
+// bytes of the reflector store: two slots per row-bulge of every stage
+size_t refl_store_bytes(const LaunchPlan& P)
+{
+    const Desc& D = P.descs[0];
+    int64_t k = 0;
+    for (int st = 0; st < D.nstages; ++st) {
+        const int bw = D.b - st * P.tune.tw, d = std::min(P.tune.tw, bw - 1);
+        k += steps_before(D.n, bw, d, D.n);
+    }
+    const size_t es = P.tune.dtype == BB_F64 ? 8 : 4;
+    return align_up((size_t)(2 * k) * (size_t)refl_stride(maxm_for(P.tune.tw)) * es);
+}
+
+template <typename T>
+int backtransform_all(const LaunchPlan& P, T* q, int64_t ldq, T* p, int64_t ldp, cudaStream_t st)
+{
+    const Desc& D = P.descs[0];
+    const int n = D.n, grid = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 152 * 16);
+    identity_kernel<T><<<grid, 256, 0, st>>>(q, ldq, n);
+    identity_kernel<T><<<grid, 256, 0, st>>>(p, ldp, n);
+    const T* refl = (const T*)P.L.refl;
+    const unsigned g2 = (unsigned)((n + 127) / 128);
+    switch (maxm_for(P.tune.tw)) {
+        case 5:
+            backtransform_kernel<T, 5><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
+            backtransform_kernel<T, 5><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            break;
+        case 9:
+            backtransform_kernel<T, 9><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
+            backtransform_kernel<T, 9><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            break;
+        case 17:
+            backtransform_kernel<T, 17><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
+            backtransform_kernel<T, 17><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            break;
+        default:
+            backtransform_kernel<T, 33><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
+            backtransform_kernel<T, 33><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            break;
+    }
+    return cudaGetLastError() == cudaSuccess ? BB_OK : BB_ERR_LAUNCH;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t band_to_bidiag_vectors_workspace_size(int64_t n, int64_t b, int dtype, const bb_tuning* tuning)
+{
+    if (dtype != BB_F32 && dtype != BB_F64) return 0;
+    const bb_tuning t = vectors_tuning(n, b, dtype, tuning);
+    bb_problem p = {n, b, (const void*)16, b + 1, (void*)16, (void*)16};
+    LaunchPlan P;
+    if (plan_launch(1, &p, dtype, &t, &P) != BB_OK) return 0;
+    return align_up(P.bytes) + refl_store_bytes(P);
+}
+
+int band_to_bidiag_vectors(int64_t n, int64_t b, int dtype, const void* band, int64_t ldab, void* d_out,
+                           void* e_out, void* q_out, int64_t ldq, void* p_out, int64_t ldp,
+                           const bb_tuning* tuning, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (dtype != BB_F32 && dtype != BB_F64) return dtype == BB_F16 || dtype == BB_BF16 ? BB_ERR_UNSUPPORTED : BB_ERR_ARG;
+    if (!q_out || !p_out || ldq < n || ldp < n) return BB_ERR_ARG;
+    const bb_tuning t = vectors_tuning(n, b, dtype, tuning);
+    bb_problem p = {n, b, band, ldab, d_out, e_out};
+    LaunchPlan P;
+    int rc = plan_launch(1, &p, dtype, &t, &P);
+    if (rc != BB_OK) return rc;
+    const size_t need = align_up(P.bytes) + refl_store_bytes(P);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (workspace_bytes < need || ((uintptr_t)ws % kAlign) != 0) return BB_ERR_WORKSPACE;
+    } else {
+        if (cudaMallocAsync(&ws, need, st) != cudaSuccess) { cudaGetLastError(); return BB_ERR_ALLOC; }
+        own = true;
+    }
+    P.L.refl = (char*)ws + align_up(P.bytes);
+    rc = enqueue(&P, ws, nullptr, st);
+    if (rc == BB_OK)
+        rc = dtype == BB_F64 ? backtransform_all<double>(P, (double*)q_out, ldq, (double*)p_out, ldp, st)
+                             : backtransform_all<float>(P, (float*)q_out, ldq, (float*)p_out, ldp, st);
     if (own) cudaFreeAsync(ws, st);
     return rc;
 }

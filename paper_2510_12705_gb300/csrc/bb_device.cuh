@@ -166,7 +166,14 @@ struct Launch {
                           // problems the group kernel takes on this stage
     int team;             // sweeps per CTA of the team kernel on the last stage
                           // (0: the per-sweep kernel runs it)
+    void* refl;           // reflector store of a single problem (compute type; nullptr: none):
+                          // slot 2 k + side (0 right, 1 left) of row-bulge k holds
+                          // v[0 .. MAXM) then tau, REFL_STRIDE(MAXM) elements a slot
+    int64_t refl_base;    // row-bulges of the stages before this launch's stage
 };
+
+// elements of one reflector slot in the store: v (MAXM) and tau, rounded to 4
+__host__ __device__ constexpr int refl_stride(int maxm) { return (maxm + 1 + 3) & ~3; }
 
 __device__ __forceinline__ const Desc& desc_of(const Launch& L, int q)
 {
@@ -198,6 +205,38 @@ __device__ __forceinline__ int find_problem_by_col(const Launch& L, int64_t c)
 // stage geometry: stage i reduces bw = b - i*tw to bw - d, d = min(tw, bw - 1)
 __device__ __forceinline__ int stage_bw(int b, int tw, int i) { return b - i * tw; }
 __device__ __forceinline__ int stage_d(int bw, int tw) { return tw < bw - 1 ? tw : bw - 1; }
+// sum_{t=0}^{T} floor(t / bw) for T >= -1
+__host__ __device__ __forceinline__ int64_t floor_sum(int64_t T, int64_t bw)
+{
+    if (T < 0) return 0;
+    const int64_t q = T / bw, r = T - q * bw;
+    return bw * q * (q - 1) / 2 + q * (r + 1);
+}
+// row-bulges of the sweeps before sweep R in stage (bw, d) of an order-n
+// problem: sweep R' has floor((a - R') / bw) + 1 of them for R' <= a, where
+// a = n - 2 - (bw - d), and none after (the count sweep_steps gives)
+__host__ __device__ __forceinline__ int64_t steps_before(int n, int bw, int d, int64_t R)
+{
+    const int64_t a = (int64_t)n - 2 - (bw - d);
+    const int64_t rc = R < a + 1 ? R : a + 1;
+    if (rc <= 0) return 0;
+    return rc + floor_sum(a, bw) - floor_sum(a - rc, bw);
+}
+
+// Store a reflector built by one warp (v[0 .. m) in shared memory, and tau)
+// into its slot of the reflector store: slot k of a launch's stage is row-bulge
+// refl_base + steps_before(n, bw, d, R) + s, side 0 (right) or 1 (left).
+template <typename T, int MAXM>
+__device__ __forceinline__ void warp_store_reflector(const Launch& L, int n, int bw, int d, int R, int s,
+                                                     int side, int m, const T* v, T tau)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t k = L.refl_base + steps_before(n, bw, d, R) + s;
+    T* slot = (T*)L.refl + (2 * k + side) * (int64_t)refl_stride(MAXM);
+    for (int t = lane; t < m; t += 32) slot[t] = v[t];
+    if (lane == 0) slot[MAXM] = tau;
+}
+
 // row-bulges of sweep R in stage (bw, d)
 __device__ __forceinline__ int sweep_steps(int n, int bw, int d, int R)
 {

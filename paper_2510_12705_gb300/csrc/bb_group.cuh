@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(384, 2) group_kernel(Launch L)
                     __syncwarp();
                     fast_reflector<T, MAXM>(m, xb, vj, tj);
                     __syncwarp();
+                    if (L.refl) warp_store_reflector<T, MAXM>(L, n, bw, d, R0 + j, s, 0, m, vj, tj[0]);
                     for (int t = lane; t < m; t += 32) V[(j + t) * PV + Ij + bw] = t == 0 ? tj[1] : (T)0;
                     if (Ij + 1 <= Ilast)
                         quad_apply_right<T, MAXM>(V, PV, bw, j, m, Ij + 1, Ilast, vj, tj[0], 0, 1);
@@ -451,6 +452,7 @@ __global__ void __launch_bounds__(384, 2) group_kernel(Launch L)
                         T* x = V + j * PV + bw + j;          // column j, rows j .. j+m-1
                         fast_reflector<T, MAXM>(m, x, vl, tl);
                         __syncwarp();
+                        if (L.refl) warp_store_reflector<T, MAXM>(L, n, bw, d, R0 + j, s, 1, m, vl, tl[0]);
                         for (int t = lane; t < m; t += 32) x[t] = t == 0 ? tl[1] : (T)0;
                         warp_publish(&s_lflag, fb + j + 1);
                     }

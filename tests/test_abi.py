@@ -281,3 +281,25 @@ def test_dense_to_band_argument_checks(bb):
     ws64 = bb.dense_to_band_workspace_size(n, b, bb.BB_F64)
     assert 8 * n * n <= ws64 <= 8 * n * n + 8 * (6 * n * b + 2 * b * b) + 4096
     assert bb.dense_to_band_workspace_size(n, b, bb.BB_F32) < ws64
+
+
+def test_vectors_entry_point_checks_and_store_size(bb):
+    """band_to_bidiag_vectors: argument checks before any GPU work, and the
+    reflector store is two slots of (MAXM + 1, rounded to 4) values per
+    row-bulge on top of the reduction's workspace."""
+    L = bb.lib()
+    fake = 0x1000
+    n, b = 300, 40
+    t = bb.Tuning(tw=16)
+    assert L.band_to_bidiag_vectors(n, b, bb.BB_F64, fake, b + 1, fake, fake, None, n, fake, n, t, None, 0,
+                                    None) == bb.BB_ERR_ARG
+    assert L.band_to_bidiag_vectors(n, b, bb.BB_F64, fake, b + 1, fake, fake, fake, n - 1, fake, n, t, None, 0,
+                                    None) == bb.BB_ERR_ARG
+    assert L.band_to_bidiag_vectors(n, b, bb.BB_F16, fake, b + 1, fake, fake, fake, n, fake, n, t, None, 0,
+                                    None) == bb.BB_ERR_UNSUPPORTED
+    assert L.band_to_bidiag_vectors_workspace_size(n, b, bb.BB_F16, t) == 0
+    base = bb.band_to_bidiag_workspace_size(n, b, bb.BB_F64, bb.Tuning(tw=16, teams=-1))
+    got = L.band_to_bidiag_vectors_workspace_size(n, b, bb.BB_F64, t)
+    steps = bb.bb_schedule_counts(n, b, 16).steps
+    store = 2 * steps * ((17 + 1 + 3) & ~3) * 8
+    assert got >= base + store and got <= base + store + 512
