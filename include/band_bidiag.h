@@ -333,6 +333,19 @@ int band_to_bidiag_vectors(int64_t n, int64_t b, int dtype, const void *band, in
 size_t dense_to_band_workspace_size(int64_t n, int64_t b, int dtype);
 int dense_to_band(int64_t n, int64_t b, int dtype, const void *a, int64_t lda, void *band_out,
                   int64_t ldab, void *workspace, size_t ws_bytes, void *stream);
+/*
+ * dense_to_band_qp -- dense_to_band (same arguments, same band, same
+ * workspace size) that also forms its orthogonal factors Q (q_out) and P
+ * (p_out), n x n, column-major, device, ldq, ldp >= n, with Q^T A P = B: each
+ * panel's block of reflectors I - V T V^T multiplies them from the right, by
+ * three GEMMs per panel and side.  With band_to_bidiag_vectors and the
+ * bidiagonal's own singular vectors this gives the singular vectors of a
+ * dense matrix.  Returns the codes of dense_to_band, BB_ERR_ARG also for NULL
+ * q_out / p_out or ldq, ldp < n.
+ */
+int dense_to_band_qp(int64_t n, int64_t b, int dtype, const void *a, int64_t lda, void *band_out,
+                     int64_t ldab, void *q_out, int64_t ldq, void *p_out, int64_t ldp, void *workspace,
+                     size_t ws_bytes, void *stream);
 
 /*
  * Singular values of the upper bidiagonal produced above (the third SVD

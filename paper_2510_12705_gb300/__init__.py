@@ -105,6 +105,7 @@ def lib():
             "band_to_bidiag_vectors_workspace_size": (sz, [i64, i64, ci, tp]),
             "band_to_bidiag_vectors": (ci, [i64, i64, ci, vp, i64, vp, vp, vp, i64, vp, i64, tp, vp, sz, vp]),
             "dense_to_band": (ci, [i64, i64, ci, vp, i64, vp, i64, vp, sz, vp]),
+            "dense_to_band_qp": (ci, [i64, i64, ci, vp, i64, vp, i64, vp, i64, vp, i64, vp, sz, vp]),
             "bb_bidiag_sigma": (ci, [i64, ci, vp, vp, vp, vp, sz, vp]),
             "bb_mlp_param_count": (sz, [ci, ci]),
             "bb_mlp_backward_scratch": (sz, [ci, ci]),
@@ -320,6 +321,27 @@ def band_to_bidiag_vectors(band, b: int, d_out, e_out, q_out, p_out, tuning=None
                                       p_out.data_ptr(), n, _tuning_ptr(tuning), ws_ptr, ws_bytes,
                                       _stream_handle(stream))
     _check(rc, "band_to_bidiag_vectors")
+
+
+def dense_to_band_qp(a, b: int, band_out, q_out, p_out, workspace=None, stream=None) -> None:
+    """dense_to_band plus its orthogonal factors: Q (q_out) and P (p_out), CUDA
+    tensors (n, n) of a's dtype holding the column-major factors (as row-major
+    tensors they read as Q^T and P^T), with Q^T A P = B for the column-major A."""
+    n = a.shape[0]
+    if a.dim() != 2 or a.shape[1] != n or not a.is_cuda or not a.is_contiguous():
+        raise ValueError("a must be a contiguous square CUDA tensor")
+    for x in (q_out, p_out):
+        if not x.is_cuda or x.dtype != a.dtype or x.shape != (n, n) or not x.is_contiguous():
+            raise ValueError("q_out and p_out must be contiguous (n, n) CUDA tensors of a's dtype")
+    if not band_out.is_cuda or band_out.dim() != 2 or band_out.shape[0] != n or band_out.dtype != a.dtype \
+            or not band_out.is_contiguous():
+        raise ValueError("band_out must be a contiguous CUDA tensor (n, ldab) of a's dtype")
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    rc = lib().dense_to_band_qp(n, b, _dtype_code(a.dtype), a.data_ptr(), n, band_out.data_ptr(), band_out.shape[1],
+                                q_out.data_ptr(), n, p_out.data_ptr(), n, ws_ptr, ws_bytes, _stream_handle(stream))
+    _check(rc, "dense_to_band_qp")
 
 
 def dense_to_band_workspace_size(n: int, b: int, dtype: int) -> int:

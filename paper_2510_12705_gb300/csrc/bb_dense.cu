@@ -259,8 +259,22 @@ cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb
 }
 
 template <typename T>
+__global__ void set_identity_kernel(T* __restrict__ X, int64_t ldx, int n)
+{
+    const int64_t total = (int64_t)n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n), i = (int)(t % n);
+        X[i + (int64_t)j * ldx] = (T)(i == j ? 1 : 0);
+    }
+}
+
+// The reduction; with Qo / Po (n x n, column-major) also the orthogonal
+// factors with Qo^T A Po = B: each panel's block of reflectors, I - V T V^T,
+// multiplies them from the right (Qo: the column panel's, on its columns
+// k .. n-1; Po: the row panel's, on its columns k+w .. n-1), in panel order.
+template <typename T>
 int dense_run(int64_t n64, int b, const T* A, int64_t lda, T* band, int64_t ldab, int64_t b_out, char* ws,
-              cudaStream_t st)
+              cudaStream_t st, T* Qo = nullptr, int64_t ldq = 0, T* Po = nullptr, int64_t ldp = 0)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BB_ERR_LAUNCH;
@@ -283,17 +297,29 @@ int dense_run(int64_t n64, int b, const T* A, int64_t lda, T* band, int64_t ldab
     const int grid1 = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 152 * 16);
     copy_matrix_kernel<T><<<grid1, 256, 0, st>>>(A, lda, Aw, n, n);
     bool ok = cudaGetLastError() == cudaSuccess;
+    if (Qo) {
+        set_identity_kernel<T><<<grid1, 256, 0, st>>>(Qo, ldq, n);
+        set_identity_kernel<T><<<grid1, 256, 0, st>>>(Po, ldp, n);
+        ok = ok && cudaGetLastError() == cudaSuccess;
+    }
     const dim3 tb(32, 8);
     for (int k = 0; ok && k < n; k += b) {
         const int m = n - k, w = std::min(b, m), n2 = n - k - w;
         panel_qr_kernel<T><<<1, PANEL_THREADS, 0, st>>>(Aw + k + (int64_t)k * n, n, m, w, w, V, n, tau);
         ok = cudaGetLastError() == cudaSuccess;
-        if (!ok || n2 <= 0) break;
-        // columns to the right: A2 <- A2 - V (T^T (V^T A2))
-        T* A2 = Aw + k + (int64_t)(k + w) * n;
+        if (!ok || (n2 <= 0 && !Qo)) break;
         ok = gemm(h, OT, ON, w, w, m, (T)1, V, n, V, n, (T)0, G, b) == CUBLAS_STATUS_SUCCESS;
         build_t_kernel<T><<<1, std::min(1024, (w + 31) / 32 * 32), 0, st>>>(G, b, tau, w, Tm, b);
         ok = ok && cudaGetLastError() == cudaSuccess;
+        if (Qo) {   // Qo[:, k:] <- Qo[:, k:] - ((Qo[:, k:] V) T) V^T
+            T* Qc = Qo + (int64_t)k * ldq;
+            ok = ok && gemm(h, ON, ON, n, w, m, (T)1, Qc, ldq, V, n, (T)0, W1, n) == CUBLAS_STATUS_SUCCESS;
+            ok = ok && gemm(h, ON, ON, n, w, w, (T)1, W1, n, Tm, b, (T)0, W2, n) == CUBLAS_STATUS_SUCCESS;
+            ok = ok && gemm(h, ON, OT, n, m, w, (T)-1, W2, n, V, n, (T)1, Qc, ldq) == CUBLAS_STATUS_SUCCESS;
+        }
+        if (!ok || n2 <= 0) break;
+        // columns to the right: A2 <- A2 - V (T^T (V^T A2))
+        T* A2 = Aw + k + (int64_t)(k + w) * n;
         ok = ok && gemm(h, OT, ON, w, n2, m, (T)1, V, n, A2, n, (T)0, W1, b) == CUBLAS_STATUS_SUCCESS;
         ok = ok && gemm(h, OT, ON, w, n2, w, (T)1, Tm, b, W1, b, (T)0, W2, b) == CUBLAS_STATUS_SUCCESS;
         ok = ok && gemm(h, ON, ON, m, n2, w, (T)-1, V, n, W2, b, (T)1, A2, n) == CUBLAS_STATUS_SUCCESS;
@@ -312,6 +338,12 @@ int dense_run(int64_t n64, int b, const T* A, int64_t lda, T* band, int64_t ldab
         ok = ok && gemm(h, ON, ON, n2, w2, n2, (T)1, A3, n, V, n, (T)0, W1, n) == CUBLAS_STATUS_SUCCESS;
         ok = ok && gemm(h, ON, ON, n2, w2, w2, (T)1, W1, n, Tm, b, (T)0, W2, n) == CUBLAS_STATUS_SUCCESS;
         ok = ok && gemm(h, ON, OT, n2, n2, w2, (T)-1, W2, n, V, n, (T)1, A3, n) == CUBLAS_STATUS_SUCCESS;
+        if (Po) {   // Po[:, k+w:] <- Po[:, k+w:] - ((Po[:, k+w:] U) T) U^T
+            T* Pc = Po + (int64_t)(k + w) * ldp;
+            ok = ok && gemm(h, ON, ON, n, w2, n2, (T)1, Pc, ldp, V, n, (T)0, W1, n) == CUBLAS_STATUS_SUCCESS;
+            ok = ok && gemm(h, ON, ON, n, w2, w2, (T)1, W1, n, Tm, b, (T)0, W2, n) == CUBLAS_STATUS_SUCCESS;
+            ok = ok && gemm(h, ON, OT, n, n2, w2, (T)-1, W2, n, V, n, (T)1, Pc, ldp) == CUBLAS_STATUS_SUCCESS;
+        }
     }
     if (!ok) return BB_ERR_LAUNCH;
     const int grid2 = (int)std::min<int64_t>(((int64_t)n * (b_out + 1) + 255) / 256, 152 * 16);
@@ -350,6 +382,34 @@ int dense_to_band(int64_t n, int64_t b, int dtype, const void* a, int64_t lda, v
     const int rc = dtype == BB_F64
         ? dense_run<double>(n, bi, (const double*)a, lda, (double*)band_out, ldab, b, (char*)ws, stream)
         : dense_run<float>(n, bi, (const float*)a, lda, (float*)band_out, ldab, b, (char*)ws, stream);
+    if (own && cudaFreeAsync(ws, stream) != cudaSuccess && rc == BB_OK) return BB_ERR_LAUNCH;
+    return rc;
+}
+
+int dense_to_band_qp(int64_t n, int64_t b, int dtype, const void* a, int64_t lda, void* band_out, int64_t ldab,
+                     void* q_out, int64_t ldq, void* p_out, int64_t ldp, void* workspace, size_t ws_bytes,
+                     void* stream_ptr)
+{
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    if (n < 1 || b < 1 || lda < n || ldab < b + 1 || !a || !band_out || !q_out || !p_out || ldq < n || ldp < n)
+        return BB_ERR_ARG;
+    if (dtype != BB_F32 && dtype != BB_F64) return dtype == BB_F16 || dtype == BB_BF16 ? BB_ERR_UNSUPPORTED : BB_ERR_ARG;
+    if (n > (int64_t)1 << 30) return BB_ERR_UNSUPPORTED;
+    const int bi = (int)std::min<int64_t>(b, n);
+    const size_t need = dense_to_band_workspace_size(n, b, dtype);
+    void* ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (ws_bytes < need) return BB_ERR_WORKSPACE;
+    } else {
+        if (cudaMallocAsync(&ws, need, stream) != cudaSuccess) { cudaGetLastError(); return BB_ERR_ALLOC; }
+        own = true;
+    }
+    const int rc = dtype == BB_F64
+        ? dense_run<double>(n, bi, (const double*)a, lda, (double*)band_out, ldab, b, (char*)ws, stream,
+                            (double*)q_out, ldq, (double*)p_out, ldp)
+        : dense_run<float>(n, bi, (const float*)a, lda, (float*)band_out, ldab, b, (char*)ws, stream,
+                           (float*)q_out, ldq, (float*)p_out, ldp);
     if (own && cudaFreeAsync(ws, stream) != cudaSuccess && rc == BB_OK) return BB_ERR_LAUNCH;
     return rc;
 }

@@ -110,3 +110,66 @@ def test_caller_workspace_and_errors():
     with pytest.raises(bb.BBError) as ei:
         bb.dense_to_band(at, b, band1, workspace=small)
     assert ei.value.code == bb.BB_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("dtype_name", ["f64", "f32"])
+@pytest.mark.parametrize("n,b", [(1, 1), (64, 16), (300, 1), (513, 64), (130, 129)])
+def test_stage1_factors(n, b, dtype_name):
+    """dense_to_band_qp: the same band as dense_to_band, and orthogonal Q, P
+    with Q^T A P = B."""
+    import torch
+    import paper_2510_12705_gb300 as bb
+    dtype = torch.float64 if dtype_name == "f64" else torch.float32
+    a = np.random.default_rng(3 * n + b).standard_normal((n, n))
+    if dtype_name == "f32":
+        a = a.astype(np.float32).astype(np.float64)
+    at = torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda", dtype)
+    band = torch.empty((n, b + 1), device="cuda", dtype=dtype)
+    q = torch.full((n, n), float("nan"), device="cuda", dtype=dtype)
+    p = torch.full((n, n), float("nan"), device="cuda", dtype=dtype)
+    bb.dense_to_band_qp(at, b, band, q, p)
+    band_ref = torch.empty((n, b + 1), device="cuda", dtype=dtype)
+    bb.dense_to_band(at, b, band_ref)
+    torch.cuda.synchronize()
+    assert torch.equal(band, band_ref)
+    bd = bandgen.dense_from_band(band.double().cpu().numpy(), b)
+    qm, pm = q.double().cpu().numpy().T, p.double().cpu().numpy().T
+    tol = TOL_F64 if dtype_name == "f64" else TOL_F32
+    eye = np.eye(n)
+    assert np.max(np.abs(qm.T @ qm - eye)) <= tol
+    assert np.max(np.abs(pm.T @ pm - eye)) <= tol
+    assert np.max(np.abs(qm.T @ a @ pm - bd)) <= tol * np.linalg.norm(a, 2)
+
+
+@pytest.mark.parametrize("dtype_name", ["f64", "f32"])
+def test_dense_svd_vectors_end_to_end(dtype_name):
+    """Singular vectors of a dense prescribed-sigma matrix: stage 1 factors
+    (dense_to_band_qp), stage 2 factors (band_to_bidiag_vectors) and the
+    bidiagonal's singular vectors (host LAPACK, test only) give A = U S V^T."""
+    import torch
+    import paper_2510_12705_gb300 as bb
+    dtype = torch.float64 if dtype_name == "f64" else torch.float32
+    n, b = 512, 32
+    a, sigma = bandgen.prescribed_sigma_dense(n, "quartercircle", seed=8)
+    if dtype_name == "f32":
+        a = a.astype(np.float32).astype(np.float64)
+    at = torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda", dtype)
+    band = torch.empty((n, b + 1), device="cuda", dtype=dtype)
+    q1 = torch.empty((n, n), device="cuda", dtype=dtype)
+    p1 = torch.empty((n, n), device="cuda", dtype=dtype)
+    q2 = torch.empty((n, n), device="cuda", dtype=dtype)
+    p2 = torch.empty((n, n), device="cuda", dtype=dtype)
+    d = torch.empty(n, device="cuda", dtype=dtype)
+    e = torch.empty(n - 1, device="cuda", dtype=dtype)
+    bb.dense_to_band_qp(at, b, band, q1, p1)
+    bb.band_to_bidiag_vectors(band, b, d, e, q2, p2)
+    torch.cuda.synchronize()
+    assert bb.bb_device_status(reset=True) == 0
+    Q = q1.double().cpu().numpy().T @ q2.double().cpu().numpy().T
+    P = p1.double().cpu().numpy().T @ p2.double().cpu().numpy().T
+    ub, s, vbt = np.linalg.svd(np.diag(d.double().cpu().numpy()) + np.diag(e.double().cpu().numpy(), 1))
+    u, v = Q @ ub, P @ vbt.T
+    tol = TOL_F64 if dtype_name == "f64" else TOL_F32
+    assert np.max(np.abs(s - np.linalg.svd(a, compute_uv=False))) <= tol * s[0]
+    assert np.max(np.abs(u @ np.diag(s) @ v.T - a)) <= tol * s[0]
+    assert np.max(np.abs(u.T @ u - np.eye(n))) <= tol and np.max(np.abs(v.T @ v - np.eye(n))) <= tol
