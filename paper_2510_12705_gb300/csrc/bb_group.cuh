@@ -26,26 +26,31 @@
 // conflicting pair is the sequential one.  3K + d <= bw keeps group g-2's step
 // s+2 out of group g's window.
 //
-// The two phases run as pipelines of warps, so that the chain of reflector
-// generations does not wait for the bulk of the updates:
-//   phase U  warp 0 builds the right reflectors in member order and applies
-//            each one itself to the rows the later members build theirs from
-//            (rows I_{j+1} .. I_{ka-1}); the other warps apply reflector j to
-//            the remaining rows above c as soon as warp 0 publishes it (a
-//            shared-memory flag), each row always in the same thread.
-//   phase L  the near warps [0, NT) run, per member, the right reflector on
-//            the rows at or below c, the left reflector (warp 0) and its
-//            update of the columns X < K+d, with team barriers; this part of
-//            the window is complete after the wait above.  Meanwhile the far
-//            warps [NT, nw) store the rows above c and publish "upper part of
-//            step s done", wait until group g-1 did the upper part of step s+1
-//            (it writes the tail columns), load the tail and the next carried
-//            block, and apply each left reflector, as it is published, to the
-//            columns X >= K+d (each column always in the same thread).
+// The two phases run as three pipelines of warps, so that the chains of
+// reflector generations do not wait for the bulk of the updates (the rows
+// above c and the rows at or below c are disjoint, so the phases overlap):
+//   warp 0       builds the right reflectors in member order and applies each
+//                one itself to the rows the later members build theirs from
+//                (rows I_{j+1} .. I_{ka-1}), then publishes it (a shared-
+//                memory flag, release / acquire at CTA scope);
+//   warps 1..NT  the near team: per member, as soon as its right reflector is
+//                published, the right reflector on the rows at or below c,
+//                the left reflector (warp 1) and its update of the columns
+//                X < K+d, with the team's named barrier; this part of the
+//                window is complete after the wait above;
+//   the rest     the far team: each right reflector, as published, on the
+//                rows I_last+1 .. -1 (each row always in the same thread);
+//                then the rows above c go back to the band and "upper part of
+//                step s done" is published; then the wait until group g-1 did
+//                the upper part of step s+1 (it writes the tail columns), the
+//                load of the tail and the next carried block, and each left
+//                reflector, as published, on the columns X >= K+d (each column
+//                always in the same thread).
 // Then all warps store the rows at or below c and publish "step s complete".
-// Every element sees the same transformations in the same order, with the
-// same arithmetic, as in the plain member-by-member program.  The host model
-// in tests/test_group_protocol.py checks the schedule element by element.
+// Every element sees the same transformations in the same order as in the
+// plain member-by-member program; the small updates on the two chains use
+// four lanes per row or column (a fixed summation order).  The host model in
+// tests/test_group_protocol.py checks the schedule element by element.
 #pragma once
 
 #include "bb_device.cuh"
@@ -64,7 +69,7 @@ __host__ __device__ __forceinline__ int group_pv(int bw, int d, int K) { return 
 __host__ __device__ __forceinline__ int group_ph(int d, int K) { return (K + d) | 1; }
 __host__ __device__ __forceinline__ int group_small_elems(int kmax, int maxm)
 {
-    // vR[kmax][maxm], tbR[kmax][4], vL[kmax][maxm], tbL[kmax][4], xb[maxm+1], ts[64], 16-byte rounding
+    // vR[kmax][maxm], tbR[kmax][4], vL[kmax][maxm], tbL[kmax][4], xb[maxm+1], 64 spare, 16-byte rounding
     return ((2 * kmax * maxm + 8 * kmax + (maxm + 1) + 64) + 3) & ~3;
 }
 // warps of the near team (warps 1 .. NT; warp 0 leads phase U, the rest are
