@@ -105,6 +105,20 @@ def oracle_sample(n, b, tw, max_steps, seed=SEED):
     return cnt["flops"], dt, cnt["steps"]
 
 
+def oracle_sample_parallel(n, b, tw, max_steps, seed=SEED):
+    """Time the OpenMP form of the oracle (the cycle schedule of Section III-A,
+    the row-bulges of each cycle on all host cores) on the first cycles that
+    hold `max_steps` row-bulges.  Returns (flops, seconds, steps, threads)."""
+    import bandgen
+    import oracle
+    ab = bandgen.random_band(n, b, seed=seed)
+    oracle.build_parallel()
+    t0 = time.perf_counter()
+    _, _, cnt, thr = oracle.band_to_bidiag_parallel(ab, b, tw, max_steps=max_steps)
+    dt = time.perf_counter() - t0
+    return cnt["flops"], dt, cnt["steps"], thr
+
+
 def reference_tw(n: int, b: int) -> int:
     """TW of our arm's FP64 configuration without touching the GPU path: the
     committed tuner weights evaluated by the FP64 MLP oracle (the library's own
@@ -451,6 +465,17 @@ def run_ours(args, rank, world):
                "seconds": dt,
                "sample": f"first {steps} row-bulges of stage 1 of the same n={n}, b={b}, TW={t64.tw} "
                          "FP64 reduction (sequential sweep order), single-threaded C oracle"}
+    cpu_par = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            flops, dt, steps, thr = oracle_sample_parallel(n, b, t64.tw, ORACLE_SAMPLE_STEPS)
+            cpu_par = {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": thr, "kind": "oracle-openmp",
+                       "seconds": dt,
+                       "sample": f"first cycles of stage 1 holding {steps} row-bulges of the same n={n}, "
+                                 f"b={b}, TW={t64.tw} FP64 reduction, cycle schedule (lag 2) with each "
+                                 f"cycle's row-bulges on {thr} OpenMP threads; bitwise the oracle's result"}
+        except (OSError, subprocess.CalledProcessError) as exc:
+            cpu_par = {"unavailable": f"OpenMP oracle build or load failed: {exc}"}
 
     if rank == 0:
         line = {
@@ -469,6 +494,7 @@ def run_ours(args, rank, world):
             "roofline": roofline,
             "fp32": fp32,
             "cpu_baseline": cpu,
+            "cpu_baseline_parallel": cpu_par,
             "e2e": e2e,
             "clocks": clk,
             # pack + the bulge-chasing launches + extract, per timed step

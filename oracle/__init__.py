@@ -11,6 +11,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never loads it and
 shares no code with it.  The reduction itself is plain C (``bulge_oracle.c``),
 compiled here with gcc, FP64, no FMA contraction, single-threaded.
+``band_to_bidiag_parallel`` runs the same row-bulges in the paper's cycle
+schedule on all host cores (OpenMP, a separate library built with
+``-fopenmp``); it is a CPU baseline, pinned bitwise to ``band_to_bidiag``.
 
 Parity status of each function:
   band_to_bidiag      pinned: closed-form Toeplitz singular values, d[0] and
@@ -35,8 +38,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bulge_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_bulge_oracle.so")
+_OMP_PATH = os.path.join(_HERE, "_bulge_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp_lib = None
 
 
 class _Counts(ctypes.Structure):
@@ -50,16 +55,25 @@ class _Counts(ctypes.Structure):
     ]
 
 
+def _compile(out: str, extra: list[str], force: bool) -> str:
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", *extra,
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the C oracle into ``oracle/_bulge_oracle.so`` (gcc, -O2,
     no FMA contraction so results do not depend on the host's FMA use)."""
-    if force or not os.path.exists(_LIB_PATH) or (
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_LIB_PATH, [], force)
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the same source with ``-fopenmp`` into
+    ``oracle/_bulge_oracle_omp.so`` (adds ``oracle_band_to_bidiag_omp``)."""
+    return _compile(_OMP_PATH, ["-fopenmp"], force)
 
 
 def _load():
@@ -82,6 +96,21 @@ def _load():
             lib.oracle_jacobi_sigma.restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+def _load_parallel():
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            build_parallel()
+            lib = ctypes.CDLL(_OMP_PATH)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_band_to_bidiag_omp.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp, dp,
+                ctypes.POINTER(_Counts), ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_band_to_bidiag_omp.restype = ctypes.c_int
+            _omp_lib = lib
+    return _omp_lib
 
 
 def _ptr(a: np.ndarray):
@@ -123,6 +152,31 @@ def band_to_bidiag(ab: np.ndarray, b: int, tw: int, *, order: int = 0,
     if return_work:
         return d, e, counts, work
     return d, e, counts
+
+
+def band_to_bidiag_parallel(ab: np.ndarray, b: int, tw: int, *, max_steps: int = -1):
+    """The reduction of ``band_to_bidiag`` in the cycle schedule of Section
+    III-A (lag 2, lag 3 on a stage that ends at bandwidth 1) with the
+    row-bulges of each cycle spread over OpenMP threads: the same d and e,
+    bit for bit.  The thread count follows ``OMP_NUM_THREADS`` (default: all
+    cores).  ``max_steps`` >= 0 stops after the cycle in which that many
+    row-bulges were done (a bounded timing sample).  Returns
+    (d, e, counts, threads)."""
+    lib = _load_parallel()
+    ab = np.ascontiguousarray(ab, dtype=np.float64)
+    n, ldab = ab.shape
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    d = np.zeros(n)
+    e = np.zeros(max(n - 1, 1))
+    cnt = _Counts()
+    thr = ctypes.c_int(0)
+    rc = lib.oracle_band_to_bidiag_omp(n, b, tw, _ptr(ab), ldab, _ptr(d), _ptr(e),
+                                       ctypes.byref(cnt), max_steps, ctypes.byref(thr))
+    if rc != 0:
+        raise ValueError(f"oracle_band_to_bidiag_omp failed: {rc}")
+    counts = {k: getattr(cnt, k) for k, _ in _Counts._fields_}
+    return d, e[: n - 1], counts, thr.value
 
 
 def bidiag_sigma(d: np.ndarray, e: np.ndarray, method: str = "auto") -> np.ndarray:

@@ -279,6 +279,97 @@ int oracle_band_to_bidiag(int n, int b, int tw, const double *ab, int ldab,
     return 0;
 }
 
+#ifdef _OPENMP
+#include <omp.h>
+/*
+ * The cycle schedule of Section III-A with the row-bulges of one cycle run in
+ * parallel: the paper's "synchronize parallel for" per cycle, on the host's
+ * cores (OpenMP threads, a barrier after every cycle).  Lag 2 on the stages
+ * whose post-stage bandwidth is at least 2 and lag 3 on a stage that ends at
+ * bandwidth 1: under these lags the row-bulges of a cycle touch disjoint
+ * elements, so the result is bitwise that of oracle_band_to_bidiag (each
+ * row-bulge is the same bulge_step; every conflicting pair keeps its order).
+ * A CPU baseline on all cores, not a reference: the tests pin it to the
+ * sequential oracle.  max_steps >= 0 stops after the cycle in which that many
+ * row-bulges were done.  *threads_used receives the thread count.
+ */
+int oracle_band_to_bidiag_omp(int n, int b, int tw, const double *ab, int ldab,
+                              double *d_out, double *e_out, oracle_counts *cnt,
+                              long long max_steps, int *threads_used)
+{
+    if (n < 1 || b < 0 || tw < 1 || ldab < b + 1 || !ab || !d_out || !cnt) return -1;
+    memset(cnt, 0, sizeof(*cnt));
+    const int b_in = b;
+    if (b > n - 1) b = n - 1;
+    band_t A;
+    A.n = n;
+    A.up = b + tw;
+    A.lo = tw;
+    A.ld = A.up + A.lo + 1;
+    A.cnt = cnt;
+    A.w = (double *)calloc((size_t)A.ld * (size_t)n, sizeof(double));
+    int *nst = (int *)malloc(sizeof(int) * (size_t)(n > 1 ? n : 1));
+    const int nthr = omp_get_max_threads();
+    oracle_counts *tc = (oracle_counts *)calloc((size_t)nthr, sizeof(oracle_counts));
+    double *vs = (double *)malloc(sizeof(double) * (size_t)(tw + 2) * (size_t)nthr);
+    if (!A.w || !nst || !tc || !vs) { free(A.w); free(nst); free(tc); free(vs); return -2; }
+    for (int j = 0; j < n; j++)
+        for (int i = (j - b > 0 ? j - b : 0); i <= j; i++)
+            *at(&A, i, j) = ab[(size_t)(b_in + i - j) + (size_t)j * (size_t)ldab];
+
+    long long done = 0;
+    int bw = b, stage = 0;
+    while (bw > 1 && (max_steps < 0 || done < max_steps)) {
+        const int d = (tw < bw - 1) ? tw : bw - 1;
+        const long long L = (bw - d >= 2) ? 2 : 3;
+        long long last = 0;
+        for (int R = 0; R < n - 1; R++) {
+            nst[R] = sweep_steps(n, bw, d, R);
+            if (nst[R] > 0 && L * R + nst[R] > last) last = L * R + nst[R];
+        }
+        long long base = done;
+        #pragma omp parallel
+        {
+            const int me = omp_get_thread_num();
+            band_t Am = A;                    /* own counters and out-of-band slot */
+            Am.cnt = &tc[me];
+            double *v = vs + (size_t)(tw + 2) * (size_t)me;
+            long long mine = base;            /* the same count in every thread */
+            for (long long t = 0; t < last; t++) {
+                if (max_steps >= 0 && mine >= max_steps) break;
+                long long rhi = t / L;
+                if (rhi > n - 2) rhi = n - 2;
+                long long rlo = rhi + 1;      /* the sweeps with a row-bulge in this cycle */
+                while (rlo - 1 >= 0 && t - L * (rlo - 1) < nst[rlo - 1]) rlo--;
+                #pragma omp for schedule(static)
+                for (long long R = rlo; R <= rhi; R++)
+                    bulge_step(&Am, bw, d, (int)R, (int)(t - L * R), v, 0);
+                mine += rhi - rlo + 1;
+            }
+            if (me == 0) done = mine;
+        }
+        bw -= d;
+        stage++;
+    }
+    for (int k = 0; k < nthr; k++) {
+        cnt->flops += tc[k].flops;
+        cnt->elements += tc[k].elements;
+        cnt->steps += tc[k].steps;
+        cnt->out_of_band += tc[k].out_of_band;
+    }
+    cnt->stages = stage;
+    for (int i = 0; i < n; i++) d_out[i] = *at(&A, i, i);
+    if (e_out)
+        for (int i = 0; i + 1 < n; i++) e_out[i] = *at(&A, i, i + 1);
+    if (threads_used) *threads_used = nthr;
+    free(A.w);
+    free(nst);
+    free(tc);
+    free(vs);
+    return 0;
+}
+#endif
+
 /*
  * Singular values of the upper bidiagonal B(d, e) by Sturm-count bisection
  * on its Golub-Kahan form: the 2n x 2n symmetric tridiagonal matrix with zero
