@@ -341,7 +341,8 @@ int dense_to_band(int64_t n, int64_t b, int dtype, const void *a, int64_t lda, v
  * three GEMMs per panel and side.  With band_to_bidiag_vectors and the
  * bidiagonal's own singular vectors this gives the singular vectors of a
  * dense matrix.  Returns the codes of dense_to_band, BB_ERR_ARG also for NULL
- * q_out / p_out or ldq, ldp < n.
+ * q_out / p_out or ldq, ldp < n, BB_ERR_UNSUPPORTED also for ldq or ldp above
+ * 2^31 - 1 (the GEMMs take 32-bit leading dimensions).
  */
 int dense_to_band_qp(int64_t n, int64_t b, int dtype, const void *a, int64_t lda, void *band_out,
                      int64_t ldab, void *q_out, int64_t ldq, void *p_out, int64_t ldp, void *workspace,

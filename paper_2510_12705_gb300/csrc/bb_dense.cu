@@ -395,6 +395,7 @@ int dense_to_band_qp(int64_t n, int64_t b, int dtype, const void* a, int64_t lda
         return BB_ERR_ARG;
     if (dtype != BB_F32 && dtype != BB_F64) return dtype == BB_F16 || dtype == BB_BF16 ? BB_ERR_UNSUPPORTED : BB_ERR_ARG;
     if (n > (int64_t)1 << 30) return BB_ERR_UNSUPPORTED;
+    if (ldq > INT32_MAX || ldp > INT32_MAX) return BB_ERR_UNSUPPORTED;   // cuBLAS takes 32-bit leading dimensions
     const int bi = (int)std::min<int64_t>(b, n);
     const size_t need = dense_to_band_workspace_size(n, b, dtype);
     void* ws = workspace;

@@ -281,6 +281,13 @@ def test_dense_to_band_argument_checks(bb):
     ws64 = bb.dense_to_band_workspace_size(n, b, bb.BB_F64)
     assert 8 * n * n <= ws64 <= 8 * n * n + 8 * (6 * n * b + 2 * b * b) + 4096
     assert bb.dense_to_band_workspace_size(n, b, bb.BB_F32) < ws64
+    big = 1 << 31
+    assert L.dense_to_band_qp(n, b, bb.BB_F64, fake, 64, fake, 9, fake, big, fake, 64, None, 0,
+                              None) == bb.BB_ERR_UNSUPPORTED
+    assert L.dense_to_band_qp(n, b, bb.BB_F64, fake, 64, fake, 9, fake, 64, fake, big, None, 0,
+                              None) == bb.BB_ERR_UNSUPPORTED
+    assert L.dense_to_band_qp(n, b, bb.BB_F64, fake, 64, fake, 9, fake, 63, fake, 64, None, 0,
+                              None) == bb.BB_ERR_ARG
 
 
 def test_vectors_entry_point_checks_and_store_size(bb):
