@@ -223,6 +223,17 @@ int bb_schedule_counts(int64_t n, int64_t b, int tw, int64_t *stages, int64_t *s
 int bb_stage_counts(int64_t n, int64_t b, int tw, int stage, int64_t *stages, int64_t *steps,
                     double *flops, double *elements);
 
+/*
+ * Order of the reflector store of band_to_bidiag_vectors (host only, no GPU
+ * needed): *k = the ordinal of step s of sweep R in stage `stage` (0-based)
+ * among all row-bulges of the reduction, counted stage by stage, sweep by
+ * sweep, step by step -- the order in which the back-transformation applies
+ * them.  Row-bulge k keeps its right reflector in slot 2k and its left one in
+ * slot 2k + 1.  Returns BB_OK, or BB_ERR_ARG for bad sizes, a NULL k or a
+ * row-bulge that the schedule does not have.
+ */
+int bb_reflector_index(int64_t n, int64_t b, int tw, int stage, int64_t R, int64_t s, int64_t *k);
+
 /* built-in default tuning for (n, b, dtype) */
 int bb_default_tuning(int64_t n, int64_t b, int dtype, bb_tuning *out);
 

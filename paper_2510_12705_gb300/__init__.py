@@ -96,6 +96,7 @@ def lib():
             "bb_default_tuning": (ci, [i64, i64, ci, tp]),
             "bb_stage_counts": (ci, [i64, i64, ci, ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+            "bb_reflector_index": (ci, [i64, i64, ci, ci, i64, i64, ctypes.POINTER(i64)]),
             "bb_measure_l2_bandwidth": (ctypes.c_double, [sz, ci, vp]),
             "bb_measure_fma_peak": (ctypes.c_double, [ci, vp]),
             "bb_autotune": (ci, [i64, i64, ci, vp, i64, vp, vp, tp, ci, ci,
@@ -272,6 +273,15 @@ def bb_schedule_counts(n: int, b: int, tw: int) -> ScheduleCounts:
     _check(lib().bb_schedule_counts(n, b, tw, ctypes.byref(st), ctypes.byref(sp),
                                     ctypes.byref(fl), ctypes.byref(el)), "bb_schedule_counts")
     return ScheduleCounts(st.value, sp.value, fl.value, el.value)
+
+
+def bb_reflector_index(n: int, b: int, tw: int, stage: int, R: int, s: int) -> int:
+    """Row-bulge ordinal k of step s of sweep R in stage `stage`: its right and
+    left reflectors sit in slots 2k and 2k + 1 of the reflector store (host
+    only; raises BBError with BB_ERR_ARG for a row-bulge that does not exist)."""
+    k = ctypes.c_int64()
+    _check(lib().bb_reflector_index(n, b, tw, stage, R, s, ctypes.byref(k)), "bb_reflector_index")
+    return k.value
 
 
 def bb_measure_l2_bandwidth(nbytes: int = 32 << 20, reps: int = 200, stream=None) -> float:

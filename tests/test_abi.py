@@ -310,3 +310,54 @@ def test_vectors_entry_point_checks_and_store_size(bb):
     steps = bb.bb_schedule_counts(n, b, 16).steps
     store = 2 * steps * ((17 + 1 + 3) & ~3) * 8
     assert got >= base + store and got <= base + store + 512
+
+
+@pytest.mark.parametrize("n,b,tw", [(1, 0, 16), (2, 1, 4), (50, 3, 2), (200, 16, 8), (300, 40, 16),
+                                    (257, 33, 32), (129, 128, 32), (97, 200, 16), (400, 64, 5)])
+def test_reflector_index_matches_generation_order(bb, n, b, tw):
+    """The slot a kernel stores a row-bulge's reflectors in (closed form:
+    earlier stages' row-bulges + earlier sweeps' + s) equals the running count
+    of the back-transformation, which walks stage by stage, sweep by sweep,
+    step by step.  A row-bulge exists while its block's first column
+    c = R + (bw - d) + s*bw has a column to its right (Section III's chase)."""
+    k = 0
+    bw, stage = min(b, n - 1), 0
+    while bw > 1:
+        d = min(tw, bw - 1)
+        for R in range(n - 1):
+            s = 0
+            while R + (bw - d) + s * bw < n - 1:
+                assert bb.bb_reflector_index(n, b, tw, stage, R, s) == k
+                k += 1
+                s += 1
+            with pytest.raises(bb.BBError):        # one past the sweep's last row-bulge
+                bb.bb_reflector_index(n, b, tw, stage, R, s)
+        bw -= d
+        stage += 1
+    assert k == bb.bb_schedule_counts(n, b, tw).steps
+    with pytest.raises(bb.BBError):                # no such stage
+        bb.bb_reflector_index(n, b, tw, stage, 0, 0)
+
+
+def test_reflector_index_at_the_bench_size(bb):
+    """n = 32768, b = 128, TW = 32: sampled sweeps against prefix sums of the
+    per-sweep row-bulge counts (same definition as above)."""
+    n, b, tw = 32768, 128, 32
+    base, bw, stage = 0, b, 0
+    rng = np.random.default_rng(0)
+    while bw > 1:
+        d = min(tw, bw - 1)
+        R = np.arange(n - 1)
+        c0 = R + (bw - d)
+        ns = np.where(c0 < n - 1, (n - 2 - c0) // bw + 1, 0)
+        before = np.concatenate([[0], np.cumsum(ns)])
+        for r in list(rng.integers(0, n - 1, 40)) + [0, n - 2 - (bw - d)]:
+            r = int(r)
+            if ns[r] == 0:
+                continue
+            for s in {0, int(ns[r]) - 1, int(ns[r]) // 2}:
+                assert bb.bb_reflector_index(n, b, tw, stage, r, s) == base + before[r] + s
+        base += int(before[-1])
+        bw -= d
+        stage += 1
+    assert base == bb.bb_schedule_counts(n, b, tw).steps
