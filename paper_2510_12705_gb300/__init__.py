@@ -163,12 +163,41 @@ def _tuning_ptr(tuning):
     return ctypes.byref(tuning)
 
 
+def _device_buffer(x, name, like=None, min_bytes=0):
+    """(pointer, bytes) of a tensor the kernels read or write: it must be a
+    contiguous CUDA tensor on `like`'s device with at least `min_bytes`
+    bytes.  A host tensor's pointer would reach a kernel as a device address,
+    so it is refused here, before any library call."""
+    if x is None or not x.is_cuda or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if like is not None and x.device != like.device:
+        raise ValueError(f"{name} must be on {like.device}, not {x.device}")
+    nbytes = x.numel() * x.element_size()
+    if nbytes < min_bytes:
+        raise ValueError(f"{name} holds {nbytes} bytes; {min_bytes} needed")
+    return x.data_ptr(), nbytes
+
+
+def _workspace_args(workspace, like):
+    """(pointer, bytes) of an optional caller workspace; (None, 0) lets the
+    library allocate its own (the library checks the size)."""
+    if workspace is None:
+        return None, 0
+    return _device_buffer(workspace, "workspace", like)
+
+
 def _check_band(band, d_out, e_out):
+    if band.dim() != 2:
+        raise ValueError("band must be a 2-D tensor (n, ldab)")
     n, ldab = band.shape
     if not (band.is_cuda and d_out.is_cuda and (n == 1 or e_out.is_cuda)):
         raise ValueError("band, d_out and e_out must be CUDA tensors")
     if not band.is_contiguous():
         raise ValueError("band must be contiguous (n, ldab)")
+    if not d_out.is_contiguous() or (n > 1 and not e_out.is_contiguous()):
+        raise ValueError("d_out and e_out must be contiguous")
+    if d_out.device != band.device or (n > 1 and e_out.device != band.device):
+        raise ValueError("band, d_out and e_out must be on one device")
     if d_out.dtype != band.dtype or (n > 1 and e_out.dtype != band.dtype):
         raise ValueError("d_out / e_out must have the band's dtype")
     if d_out.numel() < n or (n > 1 and e_out.numel() < n - 1):
@@ -187,9 +216,7 @@ def band_to_bidiag(band, b: int, d_out, e_out, stream=None) -> None:
 
 def band_to_bidiag_ex(band, b: int, d_out, e_out, tuning=None, workspace=None, stream=None):
     n, ldab = _check_band(band, d_out, e_out)
-    ws_ptr, ws_bytes = (None, 0)
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    ws_ptr, ws_bytes = _workspace_args(workspace, band)
     rc = lib().band_to_bidiag_ex(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab,
                                  d_out.data_ptr(), e_out.data_ptr() if n > 1 else None,
                                  _tuning_ptr(tuning), ws_ptr, ws_bytes, _stream_handle(stream))
@@ -303,12 +330,10 @@ def dense_to_band(a, b: int, band_out, workspace=None, stream=None) -> None:
     if a.dim() != 2 or a.shape[1] != n or not a.is_cuda or not a.is_contiguous():
         raise ValueError("a must be a contiguous square CUDA tensor")
     if not band_out.is_cuda or band_out.dim() != 2 or band_out.shape[0] != n or band_out.dtype != a.dtype \
-            or not band_out.is_contiguous():
-        raise ValueError("band_out must be a contiguous CUDA tensor (n, ldab) of a's dtype")
+            or not band_out.is_contiguous() or band_out.device != a.device:
+        raise ValueError("band_out must be a contiguous CUDA tensor (n, ldab) of a's dtype on a's device")
     code = _dtype_code(a.dtype)
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    ws_ptr, ws_bytes = _workspace_args(workspace, a)
     rc = lib().dense_to_band(n, b, code, a.data_ptr(), n, band_out.data_ptr(), band_out.shape[1],
                              ws_ptr, ws_bytes, _stream_handle(stream))
     _check(rc, "dense_to_band")
@@ -321,11 +346,10 @@ def band_to_bidiag_vectors(band, b: int, d_out, e_out, q_out, p_out, tuning=None
     that Q^T A P = bidiag(d, e); as row-major tensors they read as Q^T and P^T."""
     n, ldab = _check_band(band, d_out, e_out)
     for x in (q_out, p_out):
-        if not x.is_cuda or x.dtype != band.dtype or x.shape != (n, n) or not x.is_contiguous():
+        if not x.is_cuda or x.dtype != band.dtype or x.shape != (n, n) or not x.is_contiguous() \
+                or x.device != band.device:
             raise ValueError("q_out and p_out must be contiguous (n, n) CUDA tensors of the band's dtype")
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    ws_ptr, ws_bytes = _workspace_args(workspace, band)
     rc = lib().band_to_bidiag_vectors(n, b, _dtype_code(band.dtype), band.data_ptr(), ldab, d_out.data_ptr(),
                                       e_out.data_ptr() if n > 1 else None, q_out.data_ptr(), n,
                                       p_out.data_ptr(), n, _tuning_ptr(tuning), ws_ptr, ws_bytes,
@@ -341,14 +365,13 @@ def dense_to_band_qp(a, b: int, band_out, q_out, p_out, workspace=None, stream=N
     if a.dim() != 2 or a.shape[1] != n or not a.is_cuda or not a.is_contiguous():
         raise ValueError("a must be a contiguous square CUDA tensor")
     for x in (q_out, p_out):
-        if not x.is_cuda or x.dtype != a.dtype or x.shape != (n, n) or not x.is_contiguous():
+        if not x.is_cuda or x.dtype != a.dtype or x.shape != (n, n) or not x.is_contiguous() \
+                or x.device != a.device:
             raise ValueError("q_out and p_out must be contiguous (n, n) CUDA tensors of a's dtype")
     if not band_out.is_cuda or band_out.dim() != 2 or band_out.shape[0] != n or band_out.dtype != a.dtype \
-            or not band_out.is_contiguous():
-        raise ValueError("band_out must be a contiguous CUDA tensor (n, ldab) of a's dtype")
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+            or not band_out.is_contiguous() or band_out.device != a.device:
+        raise ValueError("band_out must be a contiguous CUDA tensor (n, ldab) of a's dtype on a's device")
+    ws_ptr, ws_bytes = _workspace_args(workspace, a)
     rc = lib().dense_to_band_qp(n, b, _dtype_code(a.dtype), a.data_ptr(), n, band_out.data_ptr(), band_out.shape[1],
                                 q_out.data_ptr(), n, p_out.data_ptr(), n, ws_ptr, ws_bytes, _stream_handle(stream))
     _check(rc, "dense_to_band_qp")
@@ -385,9 +408,8 @@ class BatchPlan:
         self.workspace_bytes = int(lib().bb_batch_plan_workspace_size(self._plan))
 
     def execute(self, workspace, stream=None):
-        rc = lib().bb_batch_execute(self._plan, workspace.data_ptr(),
-                                    workspace.numel() * workspace.element_size(),
-                                    _stream_handle(stream))
+        ws_ptr, ws_bytes = _device_buffer(workspace, "workspace", self._keep[0][0])
+        rc = lib().bb_batch_execute(self._plan, ws_ptr, ws_bytes, _stream_handle(stream))
         _check(rc, "bb_batch_execute")
 
     def __del__(self):
@@ -457,26 +479,54 @@ def bb_mlp_backward_scratch(hidden: int, N: int) -> int:
     return int(lib().bb_mlp_backward_scratch(hidden, N))
 
 
+def _mlp_buffers(in_dim: int, hidden: int, X, named):
+    """Pointers of the MLP kernels' FP32 buffers after checking that each is a
+    contiguous CUDA tensor on X's device holding what the kernels touch:
+    ``named`` maps a name to (tensor, floats needed)."""
+    import torch
+    if X.dim() != 2 or X.shape[1] != in_dim:
+        raise ValueError(f"X must be (N, {in_dim})")
+    ptrs = {}
+    for name, (t, floats) in named.items():
+        if t.dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
+        ptrs[name] = _device_buffer(t, name, X, 4 * floats)[0]
+    return ptrs
+
+
 def bb_mlp_forward(in_dim: int, hidden: int, params, X, Y, H1, H2, stream=None) -> None:
     """Y[N], H1[N][hidden], H2[N][hidden] from X[N][in_dim] (FP32 CUDA tensors)."""
-    rc = lib().bb_mlp_forward(in_dim, hidden, params.data_ptr(), X.data_ptr(), X.shape[0],
-                              Y.data_ptr(), H1.data_ptr(), H2.data_ptr(), _stream_handle(stream))
+    N, P = X.shape[0], bb_mlp_param_count(in_dim, hidden)
+    p = _mlp_buffers(in_dim, hidden, X, {"params": (params, P), "X": (X, N * in_dim), "Y": (Y, N),
+                                         "H1": (H1, N * hidden), "H2": (H2, N * hidden)})
+    rc = lib().bb_mlp_forward(in_dim, hidden, p["params"], p["X"], N, p["Y"], p["H1"], p["H2"],
+                              _stream_handle(stream))
     _check(rc, "bb_mlp_forward")
 
 
 def bb_mlp_backward(in_dim: int, hidden: int, params, X, H1, H2, Y, T, grads, scratch,
                     stream=None) -> None:
     """Gradient of mean((Y - T)^2) with respect to the flat parameters."""
-    rc = lib().bb_mlp_backward(in_dim, hidden, params.data_ptr(), X.data_ptr(), H1.data_ptr(),
-                               H2.data_ptr(), Y.data_ptr(), T.data_ptr(), X.shape[0],
-                               grads.data_ptr(), scratch.data_ptr(), _stream_handle(stream))
+    N, P = X.shape[0], bb_mlp_param_count(in_dim, hidden)
+    p = _mlp_buffers(in_dim, hidden, X, {
+        "params": (params, P), "X": (X, N * in_dim), "H1": (H1, N * hidden), "H2": (H2, N * hidden),
+        "Y": (Y, N), "T": (T, N), "grads": (grads, P),
+        "scratch": (scratch, bb_mlp_backward_scratch(hidden, N))})
+    rc = lib().bb_mlp_backward(in_dim, hidden, p["params"], p["X"], p["H1"], p["H2"], p["Y"], p["T"], N,
+                               p["grads"], p["scratch"], _stream_handle(stream))
     _check(rc, "bb_mlp_backward")
 
 
 def bb_mlp_adam(params, grads, m, v, step: int, lr: float, beta1: float = 0.9,
                 beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
-    rc = lib().bb_mlp_adam(params.numel(), params.data_ptr(), grads.data_ptr(), m.data_ptr(),
-                           v.data_ptr(), step, lr, beta1, beta2, eps, _stream_handle(stream))
+    import torch
+    count = params.numel()
+    ptrs = []
+    for name, t in (("params", params), ("grads", grads), ("m", m), ("v", v)):
+        if t.dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
+        ptrs.append(_device_buffer(t, name, params, 4 * count)[0])
+    rc = lib().bb_mlp_adam(count, *ptrs, step, lr, beta1, beta2, eps, _stream_handle(stream))
     _check(rc, "bb_mlp_adam")
 
 
@@ -487,13 +537,18 @@ def bb_bidiag_sigma(d, e, sigma_out=None, workspace=None, stream=None):
     n = d.numel()
     if e.dtype != d.dtype or (n > 1 and e.numel() < n - 1):
         raise ValueError("d and e: one dtype, len(e) >= len(d) - 1")
+    d_ptr, _ = _device_buffer(d, "d")
+    e_ptr = _device_buffer(e, "e", d)[0] if n > 1 else None
     if sigma_out is None:
         sigma_out = torch.empty(n, dtype=torch.float64, device=d.device)
+    if sigma_out.dtype != torch.float64:
+        raise ValueError("sigma_out must be float64")
+    s_ptr, _ = _device_buffer(sigma_out, "sigma_out", d, 8 * n)
     if workspace is None:
         workspace = torch.empty(int(lib().bb_bidiag_sigma_workspace_size(n)), dtype=torch.uint8,
                                 device=d.device)
-    rc = lib().bb_bidiag_sigma(n, _dtype_code(d.dtype), d.data_ptr(), e.data_ptr() if n > 1 else None,
-                               sigma_out.data_ptr(), workspace.data_ptr(),
-                               workspace.numel() * workspace.element_size(), _stream_handle(stream))
+    ws_ptr, ws_bytes = _device_buffer(workspace, "workspace", d)
+    rc = lib().bb_bidiag_sigma(n, _dtype_code(d.dtype), d_ptr, e_ptr, s_ptr, ws_ptr, ws_bytes,
+                               _stream_handle(stream))
     _check(rc, "bb_bidiag_sigma")
     return sigma_out

@@ -361,3 +361,37 @@ def test_reflector_index_at_the_bench_size(bb):
         bw -= d
         stage += 1
     assert base == bb.bb_schedule_counts(n, b, tw).steps
+
+
+def test_binding_refuses_host_tensors(bb):
+    """The Python binding passes raw pointers to the kernels, so every tensor
+    they read or write must be a CUDA tensor: host tensors (whose pointers
+    would reach a kernel as device addresses) raise ValueError before any
+    library call."""
+    import torch
+    h = torch.zeros(64, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        bb._device_buffer(h, "x")
+    with pytest.raises(ValueError):
+        bb._workspace_args(torch.zeros(16, dtype=torch.uint8), h)
+    assert bb._workspace_args(None, h) == (None, 0)
+    with pytest.raises(ValueError):
+        bb.bb_bidiag_sigma(torch.zeros(8, dtype=torch.float64), torch.zeros(7, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        bb.bb_mlp_adam(h, h, h, h, 1, 1e-3)
+    X = torch.zeros(4, 8, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        bb.bb_mlp_forward(8, 32, h, X, h, h, h)
+    with pytest.raises(ValueError):                     # X's width is not in_dim
+        bb.bb_mlp_forward(8, 32, h, torch.zeros(4, 5), h, h, h)
+    band = torch.zeros(10, 3, dtype=torch.float64)
+    d = torch.zeros(10, dtype=torch.float64)
+    e = torch.zeros(9, dtype=torch.float64)
+    for call in (lambda: bb.band_to_bidiag(band, 2, d, e),
+                 lambda: bb.band_to_bidiag_ex(band, 2, d, e),
+                 lambda: bb.band_to_bidiag_noalloc(band, 2, d, e),
+                 lambda: bb.band_to_bidiag_vectors(band, 2, d, e, torch.zeros(10, 10, dtype=torch.float64),
+                                                   torch.zeros(10, 10, dtype=torch.float64)),
+                 lambda: bb.dense_to_band(torch.zeros(10, 10, dtype=torch.float64), 2, band)):
+        with pytest.raises(ValueError):
+            call()
