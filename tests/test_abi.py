@@ -4,6 +4,7 @@ with the oracle.  No compute call reaches the GPU here."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -395,3 +396,49 @@ def test_binding_refuses_host_tensors(bb):
                  lambda: bb.dense_to_band(torch.zeros(10, 10, dtype=torch.float64), 2, band)):
         with pytest.raises(ValueError):
             call()
+
+
+_C_PROGRAM = r"""
+#include <stdio.h>
+#include "band_bidiag.h"
+int main(void) {
+    int64_t st = 0, sp = 0, k = -1;
+    double fl = 0, el = 0;
+    if (bb_schedule_counts(32768, 128, 32, &st, &sp, &fl, &el) != BB_OK) return 1;
+    if (bb_reflector_index(32768, 128, 32, 1, 5, 3, &k) != BB_OK) return 2;
+    if (band_to_bidiag(0, 4, BB_F64, 0, 5, 0, 0, 0) != BB_ERR_ARG) return 3;
+    printf("%lld %lld %.17g %.17g %lld %s\n", (long long)st, (long long)sp, fl, el, (long long)k,
+           bb_status_string(BB_ERR_ARG));
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links_from_c(bb, tmp_path):
+    """The boundary is a C ABI: the header compiles on its own as C99 and as
+    C++, and a plain C program links against the library and gets the same
+    host-side answers as the Python binding (no GPU call is made)."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    hdr = os.path.join(inc, "band_bidiag.h")
+    subprocess.check_call([gcc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Wextra", "-Werror", hdr])
+    gxx = shutil.which("g++")
+    if gxx:
+        subprocess.check_call([gxx, "-fsyntax-only", "-x", "c++", "-Wall", "-Werror", hdr])
+    src = tmp_path / "prog.c"
+    src.write_text(_C_PROGRAM)
+    libdir = os.path.dirname(bb.LIB_PATH)
+    exe = tmp_path / "prog"
+    subprocess.check_call([gcc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-L", libdir,
+                           "-lbandbidiag", f"-Wl,-rpath,{libdir}", "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    st, sp, fl, el, k, *msg = out.stdout.split()
+    ref = bb.bb_schedule_counts(32768, 128, 32)
+    assert (int(st), int(sp)) == (ref.stages, ref.steps)
+    assert float(fl) == ref.flops and float(el) == ref.elements
+    assert int(k) == bb.bb_reflector_index(32768, 128, 32, 1, 5, 3)
+    assert " ".join(msg) == bb.lib().bb_status_string(bb.BB_ERR_ARG).decode()
