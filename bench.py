@@ -177,12 +177,17 @@ def run_reference(args, rank, world):
 # was taken with and by (kernel, n, b, tw, group); a changed kernel source or
 # another configuration reports null.  Mean over the launches of that kernel
 # in one reduction (ncu dram__bytes_read.sum + dram__bytes_write.sum).
+_DRAM_085875e7 = {
+    ("group_kernel<double,double,33>", 32768, 128, 32, 24): (51286016 + 14431488 + 47294976 + 23750912
+                                                            + 39432192 + 16101888) / 3,
+    ("bulge_kernel<double,double,33>", 32768, 128, 32, 24): 34132736 + 409594112,
+}
 MEASURED_DRAM_BYTES_PER_LAUNCH: dict = {
-    "085875e7adeb6037": {
-        ("group_kernel<double,double,33>", 32768, 128, 32, 24): (51286016 + 14431488 + 47294976 + 23750912
-                                                                + 39432192 + 16101888) / 3,
-        ("bulge_kernel<double,double,33>", 32768, 128, 32, 24): 34132736 + 409594112,
-    },
+    "085875e7adeb6037": _DRAM_085875e7,
+    # the same capture: this source differs from the one above only in the
+    # back-transformation kernel of the singular vectors and its launcher,
+    # which the reduction does not run; the captured kernels' code is identical
+    "7c2b64bc09d69f4e": _DRAM_085875e7,
 }
 
 

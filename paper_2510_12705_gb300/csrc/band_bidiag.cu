@@ -504,10 +504,18 @@ __global__ void identity_kernel(T* __restrict__ X, int64_t ldx, int n)
     }
 }
 
+// The two sides are independent (blockIdx.y = 1: the left reflectors into Q,
+// 0: the right ones into P) and run in one launch; one warp per CTA spreads
+// the rows over every SM, since each row's FP64 work is a long dependent
+// chain.  The dot product keeps four partial sums to shorten that chain.
 template <typename T, int MAXM>
-__global__ void backtransform_kernel(int n, int b, int tw, int side, const T* __restrict__ refl,
-                                     T* __restrict__ X, int64_t ldx)
+__global__ void __launch_bounds__(32) backtransform_kernel(int n, int b, int tw, const T* __restrict__ refl,
+                                                           T* __restrict__ Xq, int64_t ldq, T* __restrict__ Xp,
+                                                           int64_t ldp)
 {
+    const int side = blockIdx.y;
+    T* const X = side ? Xq : Xp;
+    const int64_t ldx = side ? ldq : ldp;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     T* row = X + r;
@@ -520,21 +528,28 @@ __global__ void backtransform_kernel(int n, int b, int tw, int side, const T* __
                 const int c = R + (bw - d) + s * bw;
                 const int m = min(d + 1, n - c);
                 const T* slot = refl + (2 * k + side) * (int64_t)refl_stride(MAXM);
-                const T tau = __ldg(slot + MAXM);
-                if (tau == (T)0) continue;
-                T x[MAXM];
-                T w = (T)0;
+                T x[MAXM], v[MAXM];
 #pragma unroll
                 for (int t = 0; t < MAXM; ++t) {
                     if (t < m) {
                         x[t] = row[(int64_t)(c + t) * ldx];
-                        w = fma(x[t], __ldg(slot + t), w);
+                        v[t] = __ldg(slot + t);
                     }
                 }
-                const T f = tau * w;
+                const T tau = __ldg(slot + MAXM);
+                if (tau == (T)0) continue;
+                T w0 = (T)0, w1 = (T)0, w2 = (T)0, w3 = (T)0;
+#pragma unroll
+                for (int t = 0; t < MAXM; t += 4) {
+                    if (t < m) w0 = fma(x[t], v[t], w0);
+                    if (t + 1 < MAXM && t + 1 < m) w1 = fma(x[t + 1], v[t + 1], w1);
+                    if (t + 2 < MAXM && t + 2 < m) w2 = fma(x[t + 2], v[t + 2], w2);
+                    if (t + 3 < MAXM && t + 3 < m) w3 = fma(x[t + 3], v[t + 3], w3);
+                }
+                const T f = tau * ((w0 + w1) + (w2 + w3));
 #pragma unroll
                 for (int t = 0; t < MAXM; ++t)
-                    if (t < m) row[(int64_t)(c + t) * ldx] = fma(-f, __ldg(slot + t), x[t]);
+                    if (t < m) row[(int64_t)(c + t) * ldx] = fma(-f, v[t], x[t]);
             }
         }
         bw -= d;
@@ -1065,23 +1080,19 @@ int backtransform_all(const LaunchPlan& P, T* q, int64_t ldq, T* p, int64_t ldp,
     identity_kernel<T><<<grid, 256, 0, st>>>(q, ldq, n);
     identity_kernel<T><<<grid, 256, 0, st>>>(p, ldp, n);
     const T* refl = (const T*)P.L.refl;
-    const unsigned g2 = (unsigned)((n + 127) / 128);
+    const dim3 g2((unsigned)((n + 31) / 32), 2);
     switch (maxm_for(P.tune.tw)) {
         case 5:
-            backtransform_kernel<T, 5><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
-            backtransform_kernel<T, 5><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            backtransform_kernel<T, 5><<<g2, 32, 0, st>>>(n, D.b, P.tune.tw, refl, q, ldq, p, ldp);
             break;
         case 9:
-            backtransform_kernel<T, 9><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
-            backtransform_kernel<T, 9><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            backtransform_kernel<T, 9><<<g2, 32, 0, st>>>(n, D.b, P.tune.tw, refl, q, ldq, p, ldp);
             break;
         case 17:
-            backtransform_kernel<T, 17><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
-            backtransform_kernel<T, 17><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            backtransform_kernel<T, 17><<<g2, 32, 0, st>>>(n, D.b, P.tune.tw, refl, q, ldq, p, ldp);
             break;
         default:
-            backtransform_kernel<T, 33><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 1, refl, q, ldq);
-            backtransform_kernel<T, 33><<<g2, 128, 0, st>>>(n, D.b, P.tune.tw, 0, refl, p, ldp);
+            backtransform_kernel<T, 33><<<g2, 32, 0, st>>>(n, D.b, P.tune.tw, refl, q, ldq, p, ldp);
             break;
     }
     return cudaGetLastError() == cudaSuccess ? BB_OK : BB_ERR_LAUNCH;
