@@ -442,3 +442,24 @@ def test_header_is_plain_c_and_links_from_c(bb, tmp_path):
     assert float(fl) == ref.flops and float(el) == ref.elements
     assert int(k) == bb.bb_reflector_index(32768, 128, 32, 1, 5, 3)
     assert " ".join(msg) == bb.lib().bb_status_string(bb.BB_ERR_ARG).decode()
+
+
+@pytest.mark.parametrize("n,b,tw", [(1, 0, 16), (2, 1, 4), (100, 3, 2), (300, 40, 16), (257, 33, 32),
+                                    (2048, 128, 32)])
+def test_back_transformation_flop_count(bb, n, b, tw):
+    """bench_vectors reports the back-transformation's rate against
+    8 n * sum(m); its closed sum over the schedule equals a walk over every
+    row-bulge, and the walk's count is the schedule's row-bulge count."""
+    from paper_2510_12705_gb300.bench_vectors import reflector_length_sum
+    total, count, bw = 0, 0, min(b, n - 1)
+    while bw > 1:
+        d = min(tw, bw - 1)
+        for R in range(n - 1):
+            c = R + (bw - d)
+            while c < n - 1:
+                total += min(d + 1, n - c)
+                count += 1
+                c += bw
+        bw -= d
+    assert reflector_length_sum(n, b, tw) == total
+    assert count == bb.bb_schedule_counts(n, b, tw).steps
